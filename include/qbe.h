@@ -1,0 +1,168 @@
+/*
+ * qbe.h -- C ABI of the GB300 (sm_103a) library for the spatially
+ * inhomogeneous matrix-valued quantum Boltzmann equation of Lu & Mendl,
+ * "Numerical scheme for a spatially inhomogeneous matrix-valued quantum
+ * Boltzmann equation" (arXiv:1408.1782):
+ *
+ *     d_t W + v_x d_x W = C[W] - i [B . sigma, W]                 (eq. boltzmann)
+ *
+ * on Omega = (0,1) (one space dimension, two velocity dimensions, Sec. 2).
+ *
+ * Data conventions (all entry points):
+ *  - A state is a set of 2x2 Hermitian Wigner matrices stored as real Pauli
+ *    components w = (w0, w1, w2, w3), W = w0*1 + w1*s1 + w2*s2 + w3*s3
+ *    (Sec. 3.1, eq. spin_repr).
+ *  - Layout: double w[cell][4][ix][iy], row-major, iy fastest, with velocity
+ *    v = (2L/N) * (ix - N/2, iy - N/2), i.e. v in (2L/N) Xi with
+ *    Xi = {-N/2..N/2-1}^2 (Sec. 3.2 eq. fourier_grid, Sec. 5.1).
+ *  - Cell centres x_j = (j + 1/2)/Nx.
+ *  - Arithmetic is IEEE FP64 throughout.
+ *  - Pointers: "on_device" = 1 means the pointer is device memory of the
+ *    handle's GPU; 0 means host memory.  The caller owns every pointer it
+ *    passes; the library copies host inputs before returning and never keeps
+ *    a caller pointer.  The library owns its own device buffers.
+ *  - Calls are ordered on the handle's stream (qbe_set_stream; default: the
+ *    legacy default stream).  Calls that take or return host memory
+ *    synchronise that stream before returning; device-pointer calls are
+ *    asynchronous.
+ *  - Every entry point returns QBE_OK (0) or a negative QBE_ERR_* code; the
+ *    message of the last failure is available from qbe_last_error().  No entry
+ *    point aborts the process.
+ */
+#ifndef QBE_H
+#define QBE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QBE_OK 0
+#define QBE_ERR_ARG (-1)          /* invalid argument (size, pointer, range)        */
+#define QBE_ERR_CUDA (-2)         /* a CUDA runtime call or kernel launch failed     */
+#define QBE_ERR_ALLOC (-3)        /* device or host allocation failed                */
+#define QBE_ERR_STATE (-4)        /* call out of order (e.g. step before set_state)  */
+#define QBE_ERR_UNSUPPORTED (-5)  /* valid in the paper, not supported by this build */
+
+/* Discretisation (Sec. 3.2, Sec. 5): N velocity points per dimension (Fourier
+ * cut-off, N in {8, 16, 32, 64, 128}); Nx finite volumes; J angular points on
+ * the half circle (eq. theta_grid; even, 2..64); M Gauss-Legendre radial nodes
+ * (eq. approxH-JM; 1..64); L half-width of the periodised velocity box
+ * [-L, L]^2; R truncation radius of the collision integrals (B_R).
+ * precision must be 0 (FP64).  The paper's values are L = 12, R = 7.5,
+ * J = M = 32. */
+typedef struct qbe_grid {
+  int N;
+  int Nx;
+  int J;
+  int M;
+  double L;
+  double R;
+  int precision;
+  int device;
+} qbe_grid;
+
+/* Boundary conditions on the incoming boundary Sigma_- (Sec. 2). */
+typedef enum qbe_bc { QBE_PERIODIC = 0, QBE_DIRICHLET = 1, QBE_MAXWELL = 2 } qbe_bc;
+
+/* A Fermi-Dirac state (eq. W_FermiDirac): W_FD(v) = sum_s n_s(v) |s><s| with
+ * n_s = 1/(exp(beta (|v|^2/2 - mu_s)) + 1), |up>, |down> the columns of the
+ * unitary U (U[row][col] = U_re + i U_im), beta = 1/(k_B T) > 0. */
+typedef struct qbe_fd {
+  double beta;
+  double mu_up;
+  double mu_dn;
+  double U_re[2][2];
+  double U_im[2][2];
+} qbe_fd;
+
+typedef struct qbe_handle qbe_handle;
+
+/* Create a solver for grid g on device g->device.  Allocates the state, the
+ * kernel tables (G and H quadratures of eqs. approxG, approxH-J, approxH-JM)
+ * and the collision workspace.  *out receives the handle (NULL on failure).
+ * Errors: QBE_ERR_ARG (bad sizes, odd J, N unsupported), QBE_ERR_ALLOC,
+ * QBE_ERR_CUDA. */
+int qbe_create(const qbe_grid* g, qbe_handle** out);
+
+/* Release all device and host memory of h (NULL is ignored). */
+void qbe_destroy(qbe_handle* h);
+
+/* Message of the last failing call on h ("" if none); owned by h. */
+const char* qbe_last_error(const qbe_handle* h);
+
+/* Order all later work of h on the CUDA stream `stream` (a cudaStream_t, may
+ * be NULL for the legacy default stream). */
+int qbe_set_stream(qbe_handle* h, void* stream);
+
+/* Boundary condition (Sec. 2): QBE_PERIODIC (left/right ignored), QBE_DIRICHLET
+ * (incoming values are the Fermi-Dirac states *left at x = 0, *right at x = 1),
+ * QBE_MAXWELL (R = (1 - alpha) L + alpha D with diffusive states *left, *right,
+ * accommodation alpha in [0, 1]).  Default after create: periodic.
+ * Errors: QBE_ERR_ARG (bad kind, NULL state for D/M, beta <= 0, alpha out of
+ * [0,1]). */
+int qbe_set_boundary(qbe_handle* h, int bc, const qbe_fd* left, const qbe_fd* right, double alpha);
+
+/* External magnetic field B[cell][3] at the cell centres (eq. boltzmann).
+ * Default after create: zero. */
+int qbe_set_bfield(qbe_handle* h, const double* B, int on_device);
+
+/* Copy a state w[Nx][4][N][N] into the solver / out of the solver. */
+int qbe_set_state(qbe_handle* h, const double* w, int on_device);
+int qbe_get_state(qbe_handle* h, double* w, int on_device);
+
+/* Collision operator C[W] = C_c[W] + C_d[W] (eqs. Cc, Cd in the Pauli form
+ * eq. CcPauli, eq. CdPauli) by the fast Fourier spectral method of Sec. 3.2
+ * (Carleman representation, quadratures G_J, H_J, H_JM, double zero padding),
+ * for ncells independent cells: w[ncells][4][N][N] -> c[ncells][4][N][N].
+ * Does not touch the solver state.  The -N/2 Fourier line (no +N/2 partner in
+ * Xi) is excluded from input and output so that every field is real.
+ * Errors: QBE_ERR_ARG (ncells < 1, NULL pointers). */
+int qbe_collide(qbe_handle* h, const double* w, double* c, int ncells, int on_device);
+
+/* Transport operator A(tau) on the solver state: the minmod slope-limiter
+ * finite-volume update of eq. slopeLimiterStep applied per velocity and per
+ * Pauli component (eq. minmod), with two ghost cells per side filled from the
+ * boundary condition, sub-cycled so that |v_x| tau_sub / dx <= 1 (Sec. 4).
+ * Errors: QBE_ERR_STATE (no state set). */
+int qbe_advect(qbe_handle* h, double tau);
+
+/* Collision + precession substep of length dt on the solver state: Heun's
+ * second-order Runge-Kutta method for dW/dt = C[W] + 2 (B x w).sigma
+ * (eq. boltzmann; -i[B.sigma, W] in Pauli form, Sec. 3.1). */
+int qbe_collide_rk2(qbe_handle* h, double dt);
+
+/* nsteps split time steps A(dt/2) o RK2[C + B](dt) o A(dt/2) (Sec. 4). */
+int qbe_step(qbe_handle* h, double dt, int nsteps);
+
+/* Moments of the solver state per cell (eqs. density, velocity,
+ * internal_energy): rho[Nx][4] = Pauli components of int W dv,
+ * mom[Nx][2] = int v tr W dv, energy[Nx] = int |v|^2/2 tr W dv, all as grid
+ * sums times (2L/N)^2.  Any output pointer may be NULL. */
+int qbe_moments(qbe_handle* h, double* rho, double* mom, double* energy, int on_device);
+
+/* Number of kernel launches issued by the library since create (for
+ * benchmarking bookkeeping). */
+long long qbe_launch_count(const qbe_handle* h);
+
+/* Device-time accounting per kernel group (diagnostics; not part of the
+ * method).  qbe_enable_timing(h, 1) clears the counters and brackets every
+ * later launch of the library with CUDA events on h's stream;
+ * qbe_kernel_time() synchronises the stream and returns the accumulated
+ * device time (ms) and launch count of one group since enabling.  Groups:
+ * 0 coefficients/prep, 1 I1 (C_c), 2 I2+I4, 3 I3 (Hu-Ying term),
+ * 4 assembly/projection, 5 transport, 6 RK/precession update. */
+#define QBE_KG_PREP 0
+#define QBE_KG_I1 1
+#define QBE_KG_I24 2
+#define QBE_KG_I3 3
+#define QBE_KG_ASSEMBLE 4
+#define QBE_KG_TRANSPORT 5
+#define QBE_KG_RK 6
+int qbe_enable_timing(qbe_handle* h, int enable);
+int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QBE_H */

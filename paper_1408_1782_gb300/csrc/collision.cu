@@ -1,0 +1,70 @@
+// Size dispatch and workspace allocation of the collision operator; the
+// kernels are instantiated per fine-grid size in collision_n*.cu.
+#include "internal.h"
+
+namespace qbe {
+
+cudaError_t collide_batch(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells,
+                          cudaStream_t s, long long& launches, KernelTimer* tm) {
+  switch (t.n) {
+    case 16: return collide_batch_n<16>(t, cw, w, c, ncells, s, launches, tm);
+    case 32: return collide_batch_n<32>(t, cw, w, c, ncells, s, launches, tm);
+    case 64: return collide_batch_n<64>(t, cw, w, c, ncells, s, launches, tm);
+    case 128: return collide_batch_n<128>(t, cw, w, c, ncells, s, launches, tm);
+    case 256: return collide_batch_n<256>(t, cw, w, c, ncells, s, launches, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+
+cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw) {
+  const size_t P = (size_t)t.n * t.n;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int bps = 1;
+  switch (t.n) {
+    case 16: bps = i3_blocks_per_sm<16>(); break;
+    case 32: bps = i3_blocks_per_sm<32>(); break;
+    case 64: bps = i3_blocks_per_sm<64>(); break;
+    case 128: bps = i3_blocks_per_sm<128>(); break;
+    case 256: bps = i3_blocks_per_sm<256>(); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cw.nb = nb;
+  cw.grid_i3 = nsm * bps;
+  // enough (cell, j, m-chunk) units for about 8 waves of the persistent grid
+  int nmc = (8 * cw.grid_i3 + nb * t.J - 1) / (nb * t.J);
+  if (nmc < 1) nmc = 1;
+  if (nmc > t.M) nmc = t.M;
+  cw.mch = (t.M + nmc - 1) / nmc;
+  cw.nmc = (t.M + cw.mch - 1) / cw.mch;
+  const size_t nparts = (size_t)nb * t.J * cw.nmc;
+  cw.ws_slots = nb > cw.grid_i3 ? nb : cw.grid_i3;
+  size_t ws_fields = 6 * (size_t)nb;
+  if (3 * (size_t)cw.grid_i3 > ws_fields) ws_fields = 3 * (size_t)cw.grid_i3;
+  cw.ws_fields = ws_fields;
+  const size_t N = t.N;
+  cudaError_t e;
+#define QBE_ALLOC(ptr, bytes) \
+  if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) { free_collision_work(cw); return e; }
+  QBE_ALLOC(cw.what, (size_t)nb * 4 * P * sizeof(double2));
+  QBE_ALLOC(cw.wfine, (size_t)nb * 2 * P * sizeof(double2));
+  QBE_ALLOC(cw.Dacc, (size_t)nb * 2 * P * sizeof(double2));
+  QBE_ALLOC(cw.K2acc, (size_t)nb * P * sizeof(double));
+  QBE_ALLOC(cw.K4acc, (size_t)nb * 2 * P * sizeof(double2));
+  QBE_ALLOC(cw.K3part, nparts * 2 * P * sizeof(double2));
+  QBE_ALLOC(cw.ws, ws_fields * P * sizeof(double2));
+  QBE_ALLOC(cw.cbuf, (size_t)nb * 4 * N * N * sizeof(double));
+  QBE_ALLOC(cw.wbuf, (size_t)nb * 4 * N * N * sizeof(double));
+#undef QBE_ALLOC
+  return cudaSuccess;
+}
+
+void free_collision_work(CollisionWork& cw) {
+  cudaFree(cw.what); cudaFree(cw.wfine); cudaFree(cw.Dacc); cudaFree(cw.K2acc); cudaFree(cw.K4acc);
+  cudaFree(cw.K3part); cudaFree(cw.ws); cudaFree(cw.cbuf); cudaFree(cw.wbuf);
+  cw = CollisionWork();
+}
+
+}  // namespace qbe

@@ -1,0 +1,255 @@
+// Block-level FFT building blocks for the spectral collision operator.
+//
+// A length-n DFT (n = A*B) is done in two in-place stages on a line of
+// double2 values (Cooley-Tukey "four-step" split, no reordering pass):
+//   t = B*t1 + t2,  k = k1 + A*k2
+//   forward: X[k1 + A k2] = sum_t2 e^{-2pi i t2 k2/B} [ e^{-2pi i t2 k1/n} sum_t1 e^{-2pi i t1 k1/A} x[B t1 + t2] ]
+// Stage 1 reads positions B*t1 + t2 and writes back to the same positions
+// (holding index k1 at B*k1 + t2); stage 2 reads the B contiguous values at
+// B*k1 + (0..B-1) and writes them back in place.  The spectrum therefore sits
+// in the "permuted" order pos(k) = B*(k mod A) + (k div A).  The inverse runs
+// the two stages backwards and takes permuted input to natural output.  All
+// spectral-space tables of the library are stored in this permuted order.
+//
+// Sign convention: forward = sum x e^{-2 pi i ...}, inverse = sum X e^{+2 pi i ...},
+// both unnormalised.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace qbe {
+
+template <int n> struct Split;
+template <> struct Split<16>  { static constexpr int A = 4,  B = 4;  };
+template <> struct Split<32>  { static constexpr int A = 4,  B = 8;  };
+template <> struct Split<64>  { static constexpr int A = 8,  B = 8;  };
+template <> struct Split<128> { static constexpr int A = 8,  B = 16; };
+template <> struct Split<256> { static constexpr int A = 16, B = 16; };
+
+// Frequency index (0..n-1, standard wrap) stored at permuted position pos.
+template <int n>
+__host__ __device__ __forceinline__ int freq_of_pos(int pos) {
+  constexpr int A = Split<n>::A, B = Split<n>::B;
+  return pos / B + A * (pos % B);
+}
+// Permuted position of frequency index k.
+template <int n>
+__host__ __device__ __forceinline__ int pos_of_freq(int k) {
+  constexpr int A = Split<n>::A, B = Split<n>::B;
+  return B * (k % A) + k / A;
+}
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// cos(2 pi k / 16) for integer k (mathematical constants cos(pi/8), sin(pi/8), sqrt(1/2)).
+__host__ __device__ constexpr double cos16(int k) {
+  constexpr double c1 = 0.92387953251128675613;   // cos(pi/8)
+  constexpr double s1 = 0.38268343236508977173;   // sin(pi/8)
+  constexpr double r2 = 0.70710678118654752440;   // sqrt(1/2)
+  k &= 15;
+  return k == 0 ? 1.0 : k == 1 ? c1 : k == 2 ? r2 : k == 3 ? s1 : k == 4 ? 0.0 : k == 5 ? -s1
+       : k == 6 ? -r2 : k == 7 ? -c1 : k == 8 ? -1.0 : k == 9 ? -c1 : k == 10 ? -r2 : k == 11 ? -s1
+       : k == 12 ? 0.0 : k == 13 ? s1 : k == 14 ? r2 : c1;
+}
+__host__ __device__ constexpr double sin16(int k) { return cos16(k - 4); }
+
+// x * exp(SIGN * 2 pi i k / R) for R <= 16, k a compile-time constant after unrolling.
+template <int R, int SIGN>
+__device__ __forceinline__ double2 twid(int k, double2 x) {
+  const int k16 = (k * (16 / R)) & 15;
+  if (k16 == 0) return x;
+  if (k16 == 8) return make_double2(-x.x, -x.y);
+  if (k16 == 4) return SIGN > 0 ? make_double2(-x.y, x.x) : make_double2(x.y, -x.x);
+  if (k16 == 12) return SIGN > 0 ? make_double2(x.y, -x.x) : make_double2(-x.y, x.x);
+  const double c = cos16(k16), s = SIGN * sin16(k16);
+  return make_double2(fma(x.x, c, -x.y * s), fma(x.x, s, x.y * c));
+}
+
+__host__ __device__ constexpr int ilog2c(int r) { return r <= 1 ? 0 : 1 + ilog2c(r / 2); }
+// Bit reversal of i within `bits` <= 4 bits (closed form so that it folds after unrolling).
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+  return (((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3)) >> (4 - bits);
+}
+
+// One radix-2 decimation-in-time stage of butterfly span S on R registers.
+template <int R, int SIGN, int S>
+struct DftStage {
+  __device__ __forceinline__ static void run(double2 (&b)[R]) {
+#pragma unroll
+    for (int g = 0; g < R; g += S) {
+#pragma unroll
+      for (int k = 0; k < S / 2; ++k) {
+        const double2 t = twid<16, SIGN>(k * (16 / S), b[g + k + S / 2]);
+        const double2 u = b[g + k];
+        b[g + k] = cadd(u, t);
+        b[g + k + S / 2] = csub(u, t);
+      }
+    }
+    DftStage<R, SIGN, 2 * S>::run(b);
+  }
+};
+template <int R, int SIGN>
+struct DftStage<R, SIGN, 2 * R> {
+  __device__ __forceinline__ static void run(double2 (&)[R]) {}
+};
+
+// In-register DFT of length R <= 16 (natural order in and out).
+template <int R, int SIGN>
+__device__ __forceinline__ void dft(double2 (&a)[R]) {
+  constexpr int L2 = ilog2c(R);
+  double2 b[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) b[i] = a[bitrev(i, L2)];
+  DftStage<R, SIGN, 2>::run(b);
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[i] = b[i];
+}
+
+// FFT of nl lines of length n held in shared (or global) memory:
+// element e of line l at buf[l*ls + e*es].  tw[t2*A + k1] = exp(-2 pi i t2 k1 / n).
+// SIGN < 0: forward, natural -> permuted.  SIGN > 0: inverse, permuted -> natural.
+// Must be called by every thread of the block; ends with __syncthreads().
+template <int n, int SIGN>
+__device__ __forceinline__ void fft_lines(double2* buf, int nl, int ls, int es, const double2* __restrict__ tw) {
+  constexpr int A = Split<n>::A, B = Split<n>::B;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (SIGN < 0) {
+    for (int task = tid; task < nl * B; task += nt) {
+      const int l = task % nl, t2 = task / nl;
+      double2* base = buf + l * ls + t2 * es;
+      double2 a[A];
+#pragma unroll
+      for (int t1 = 0; t1 < A; ++t1) a[t1] = base[B * t1 * es];
+      dft<A, -1>(a);
+#pragma unroll
+      for (int k1 = 1; k1 < A; ++k1) a[k1] = cmul(a[k1], tw[t2 * A + k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) base[B * k1 * es] = a[k1];
+    }
+    __syncthreads();
+    for (int task = tid; task < nl * A; task += nt) {
+      const int l = task % nl, k1 = task / nl;
+      double2* base = buf + l * ls + B * k1 * es;
+      double2 b[B];
+#pragma unroll
+      for (int t2 = 0; t2 < B; ++t2) b[t2] = base[t2 * es];
+      dft<B, -1>(b);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) base[k2 * es] = b[k2];
+    }
+    __syncthreads();
+  } else {
+    for (int task = tid; task < nl * A; task += nt) {
+      const int l = task % nl, k1 = task / nl;
+      double2* base = buf + l * ls + B * k1 * es;
+      double2 b[B];
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) b[k2] = base[k2 * es];
+      dft<B, 1>(b);
+#pragma unroll
+      for (int t2 = 0; t2 < B; ++t2) base[t2 * es] = b[t2];
+    }
+    __syncthreads();
+    for (int task = tid; task < nl * B; task += nt) {
+      const int l = task % nl, t2 = task / nl;
+      double2* base = buf + l * ls + t2 * es;
+      double2 a[A];
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) a[k1] = base[B * k1 * es];
+#pragma unroll
+      for (int k1 = 1; k1 < A; ++k1) a[k1] = cmulc(a[k1], tw[t2 * A + k1]);
+      dft<A, 1>(a);
+#pragma unroll
+      for (int t1 = 0; t1 < A; ++t1) base[B * t1 * es] = a[t1];
+    }
+    __syncthreads();
+  }
+}
+
+// Chunk sizes (rows per row-pass chunk, columns per column-pass chunk) so that a
+// chunk of complex doubles occupies about 32 KB of shared memory.
+template <int n> struct Chunk {
+  static constexpr int RC = (n >= 256) ? 8 : (n >= 128) ? 16 : (n >= 64) ? 32 : n;
+  static constexpr int CC = RC;
+  static constexpr int LS = n + 1;                 // padded row stride (odd => no bank conflicts)
+  static constexpr int SMEM_ELEMS = (RC * LS > CC * n ? RC * LS : CC * n);
+};
+
+// Row pass over an n x n field (rows = fixed ix, transform along iy):
+// for each chunk: sm[r][iy] = ld(ix, iy); [FFT DIR1]; [sm = mid(ix, iy, sm)]; [FFT DIR2]; st(ix, iy, sm).
+// DIR = 0 skips that transform; HAS_MID selects the pointwise middle step.
+template <int n, int DIR1, bool HAS_MID, int DIR2, class LD, class MID, class ST>
+__device__ __forceinline__ void row_pass(double2* sm, const double2* tw, LD ld, MID mid, ST st) {
+  constexpr int RC = Chunk<n>::RC, LS = Chunk<n>::LS;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int r0 = 0; r0 < n; r0 += RC) {
+    for (int idx = tid; idx < RC * n; idx += nt) {
+      const int r = idx / n, iy = idx % n;
+      sm[r * LS + iy] = ld(r0 + r, iy);
+    }
+    __syncthreads();
+    if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1)>(sm, RC, LS, 1, tw);
+    if (HAS_MID) {
+      for (int idx = tid; idx < RC * n; idx += nt) {
+        const int r = idx / n, iy = idx % n;
+        sm[r * LS + iy] = mid(r0 + r, iy, sm[r * LS + iy]);
+      }
+      __syncthreads();
+    }
+    if (DIR2 != 0) fft_lines<n, (DIR2 < 0 ? -1 : 1)>(sm, RC, LS, 1, tw);
+    for (int idx = tid; idx < RC * n; idx += nt) {
+      const int r = idx / n, iy = idx % n;
+      st(r0 + r, iy, sm[r * LS + iy]);
+    }
+    __syncthreads();
+  }
+}
+
+// Column pass (transform along ix) over chunks of CC columns held as sm[ix][c].
+template <int n, int DIR1, bool HAS_MID, int DIR2, class LD, class MID, class ST>
+__device__ __forceinline__ void col_pass(double2* sm, const double2* tw, LD ld, MID mid, ST st) {
+  constexpr int CC = Chunk<n>::CC;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c0 = 0; c0 < n; c0 += CC) {
+    for (int idx = tid; idx < CC * n; idx += nt) {
+      const int ix = idx / CC, c = idx % CC;
+      sm[ix * CC + c] = ld(ix, c0 + c);
+    }
+    __syncthreads();
+    if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1)>(sm, CC, 1, CC, tw);
+    if (HAS_MID) {
+      for (int idx = tid; idx < CC * n; idx += nt) {
+        const int ix = idx / CC, c = idx % CC;
+        sm[ix * CC + c] = mid(ix, c0 + c, sm[ix * CC + c]);
+      }
+      __syncthreads();
+    }
+    if (DIR2 != 0) fft_lines<n, (DIR2 < 0 ? -1 : 1)>(sm, CC, 1, CC, tw);
+    for (int idx = tid; idx < CC * n; idx += nt) {
+      const int ix = idx / CC, c = idx % CC;
+      st(ix, c0 + c, sm[ix * CC + c]);
+    }
+    __syncthreads();
+  }
+}
+
+struct NoMid {
+  __device__ double2 operator()(int, int, double2 v) const { return v; }
+};
+
+// Load the n-point twiddle table into shared memory.
+template <int n>
+__device__ __forceinline__ void load_twiddles(double2* sm_tw, const double2* __restrict__ g_tw) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sm_tw[i] = g_tw[i];
+  __syncthreads();
+}
+
+}  // namespace qbe

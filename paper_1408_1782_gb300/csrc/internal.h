@@ -1,0 +1,136 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qbe.h"
+
+namespace qbe {
+
+// Device-side kernel tables for one grid (all spectral tables in the permuted
+// order of the line FFT, see fft.cuh).
+struct Tables {
+  int N = 0, n = 0, J = 0, M = 0;
+  double L = 0, R = 0;
+  double2* tw = nullptr;        // [n]      exp(-2 pi i t2 k1 / n), index t2*A + k1
+  double* phip = nullptr;       // [J][n*n] phi_R(sigma . theta'_j)                       (eq. approxG)
+  double* Ktab = nullptr;       // [J][n*n] sum_j omega_G[j][j'] phi_R(sigma.theta_j) / n^2 (eq. approxG)
+  double* psi = nullptr;        // [J][n*n] psi_R(sigma . theta_j)                        (eq. approxH-J)
+  double* psip_s = nullptr;     // [J][n*n] psi_R(sigma . theta_j^perp) / n^2              (eq. approxH-J)
+  double2* phase = nullptr;     // [J*M][2][n] sqrt(pi w_m / J) e^{i alpha_x sigma_x}, e^{i alpha_y sigma_y} (eq. approxH-JM)
+};
+
+// Per-evaluation buffers of the collision operator for a batch of nb cells.
+struct CollisionWork {
+  int nb = 0;          // cells per batch
+  int nmc = 1;         // m-chunks per (cell, j) unit of the I3 kernel
+  int mch = 1;         // m values per chunk
+  int grid_i3 = 0;     // persistent grid of the I3 kernel
+  double2* what = nullptr;   // [nb][4][n*n] spectral pairs (w0+iw1, w2+iw3, w1+iw2, w3)
+  double2* wfine = nullptr;  // [nb][2][n*n] fine-grid fields (w0+iw1, w2+iw3)
+  double2* Dacc = nullptr;   // [nb][2][n*n] spectral D (pairs (1,2), (3,-))
+  double* K2acc = nullptr;   // [nb][n*n]
+  double2* K4acc = nullptr;  // [nb][2][n*n] spectral K4 pairs (0,1), (2,3)
+  double2* K3part = nullptr; // [nb*J*nmc][2][n*n] fine-grid K3 pair partial sums
+  double2* ws = nullptr;     // per-CTA scratch
+  size_t ws_fields = 0;      // complex n*n fields of scratch per CTA slot
+  int ws_slots = 0;          // number of CTA slots in ws
+  double* cbuf = nullptr;    // [nb][4][N][N] staging for collide in/out
+  double* wbuf = nullptr;
+};
+
+// Launch configuration helpers.
+constexpr int kThreads = 256;
+
+// Kernel groups for the per-kernel device-time accounting (qbe_kernel_time).
+enum KernelGroup { KG_PREP = 0, KG_I1 = 1, KG_I24 = 2, KG_I3 = 3, KG_ASSEMBLE = 4, KG_TRANSPORT = 5, KG_RK = 6,
+                   KG_COUNT = 7 };
+
+// Brackets launches with CUDA events on their stream when enabled; the events
+// are resolved (and the stream synchronised) only in collect().
+struct KernelTimer {
+  bool on = false;
+  struct Pending {
+    int which;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  double total_ms[KG_COUNT] = {};
+  long long count[KG_COUNT] = {};
+  void begin(int which, cudaStream_t s) {
+    if (!on) return;
+    Pending p{which, nullptr, nullptr};
+    cudaEventCreate(&p.a);
+    cudaEventCreate(&p.b);
+    cudaEventRecord(p.a, s);
+    pending.push_back(p);
+  }
+  void end(cudaStream_t s) {
+    if (!on || pending.empty()) return;
+    cudaEventRecord(pending.back().b, s);
+  }
+  cudaError_t collect() {
+    cudaError_t err = cudaSuccess;
+    for (auto& p : pending) {
+      float ms = 0.f;
+      cudaError_t e = cudaEventSynchronize(p.b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+      if (e == cudaSuccess) {
+        total_ms[p.which] += ms;
+        count[p.which] += 1;
+      } else {
+        err = e;
+      }
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    pending.clear();
+    return err;
+  }
+  void reset() {
+    collect();
+    for (int i = 0; i < KG_COUNT; ++i) { total_ms[i] = 0; count[i] = 0; }
+  }
+};
+
+// Host-side table construction (tables.cpp).
+bool build_tables(int N, int J, int M, double L, double R, Tables& t, std::string& err);
+void free_tables(Tables& t);
+
+// Wall Fermi-Dirac state in Pauli form on the coarse grid [4][N][N] (eq. W_FermiDirac).
+void fermi_dirac_pauli(const qbe_fd& fd, int N, double L, std::vector<double>& out);
+
+// Collision operator on a batch (collision.cu).  w, c: device [nb][4][N][N].
+cudaError_t collide_batch(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells,
+                          cudaStream_t s, long long& launches, KernelTimer* tm);
+cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw);
+template <int n>
+cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells, cudaStream_t s,
+                            long long& launches, KernelTimer* tm);
+template <int n>
+int i3_blocks_per_sm();
+void free_collision_work(CollisionWork& cw);
+
+// Transport, precession/RK and moments (transport.cu).
+struct BoundaryDev {
+  int kind = QBE_PERIODIC;
+  double alpha = 0.0;
+  double* phiL = nullptr;   // [4][N][N] wall state at x = 0
+  double* phiR = nullptr;   // [4][N][N] wall state at x = 1
+  double ZL = 1.0, ZR = 1.0;
+  double* fbar = nullptr;   // [2] outgoing number fluxes (device scratch)
+};
+
+cudaError_t advect_substep(const double* Win, double* Wout, int Nx, int N, double L, double tau,
+                           const BoundaryDev& bc, cudaStream_t s, long long& launches, KernelTimer* tm);
+cudaError_t rk_stage1(const double* W, const double* C, const double* B, double dt, double* F0, double* W1,
+                      int Nx, int N, cudaStream_t s, long long& launches, KernelTimer* tm);
+cudaError_t rk_stage2(const double* W, const double* F0, const double* C1, const double* W1, const double* B,
+                      double dt, double* Wout, int Nx, int N, cudaStream_t s, long long& launches, KernelTimer* tm);
+cudaError_t moments_launch(const double* W, int Nx, int N, double L, double* out7, cudaStream_t s,
+                           long long& launches);
+
+}  // namespace qbe

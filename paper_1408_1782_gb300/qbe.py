@@ -1,0 +1,216 @@
+"""Thin Python binding of the C ABI in include/qbe.h (argument marshalling only).
+
+Every computation runs in the sm_103a kernels of ``libqbe.so``; there is no
+CPU fallback.  If the library has not been built, importing ``lib()`` raises.
+
+Arrays: numpy float64 arrays are passed as host memory (the library copies
+them); CUDA torch tensors (float64, contiguous) are passed as device memory.
+State layout: ``w[cell][4][ix][iy]`` Pauli components, v = (2L/N)(ix-N/2, iy-N/2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqbe.so")
+
+QBE_PERIODIC, QBE_DIRICHLET, QBE_MAXWELL = 0, 1, 2
+_BC = {"periodic": QBE_PERIODIC, "dirichlet": QBE_DIRICHLET, "maxwell": QBE_MAXWELL}
+
+# Every entry point declared in include/qbe.h, with its ctypes signature.
+_c_int, _c_double, _c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+class QbeGrid(ctypes.Structure):
+    _fields_ = [("N", _c_int), ("Nx", _c_int), ("J", _c_int), ("M", _c_int), ("L", _c_double),
+                ("R", _c_double), ("precision", _c_int), ("device", _c_int)]
+
+
+class QbeFD(ctypes.Structure):
+    _fields_ = [("beta", _c_double), ("mu_up", _c_double), ("mu_dn", _c_double),
+                ("U_re", (_c_double * 2) * 2), ("U_im", (_c_double * 2) * 2)]
+
+
+SIGNATURES = {
+    "qbe_create": (_c_int, [ctypes.POINTER(QbeGrid), ctypes.POINTER(_c_void_p)]),
+    "qbe_destroy": (None, [_c_void_p]),
+    "qbe_last_error": (ctypes.c_char_p, [_c_void_p]),
+    "qbe_set_stream": (_c_int, [_c_void_p, _c_void_p]),
+    "qbe_set_boundary": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(QbeFD), ctypes.POINTER(QbeFD), _c_double]),
+    "qbe_set_bfield": (_c_int, [_c_void_p, _c_void_p, _c_int]),
+    "qbe_set_state": (_c_int, [_c_void_p, _c_void_p, _c_int]),
+    "qbe_get_state": (_c_int, [_c_void_p, _c_void_p, _c_int]),
+    "qbe_collide": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_int]),
+    "qbe_advect": (_c_int, [_c_void_p, _c_double]),
+    "qbe_collide_rk2": (_c_int, [_c_void_p, _c_double]),
+    "qbe_step": (_c_int, [_c_void_p, _c_double, _c_int]),
+    "qbe_moments": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int]),
+    "qbe_launch_count": (ctypes.c_longlong, [_c_void_p]),
+    "qbe_enable_timing": (_c_int, [_c_void_p, _c_int]),
+    "qbe_kernel_time": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)]),
+}
+
+KERNEL_GROUPS = {"prep": 0, "i1": 1, "i24": 2, "i3": 3, "assemble": 4, "transport": 5, "rk": 6}
+
+_lib = None
+
+
+class QbeError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libqbe.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise QbeError(f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def fd_state(beta, mu_up, mu_dn, U=None) -> QbeFD:
+    """Fermi-Dirac wall state; U: 2x2 complex unitary, columns = spin basis (default identity)."""
+    U = np.eye(2) if U is None else np.asarray(U, dtype=np.complex128)
+    f = QbeFD()
+    f.beta, f.mu_up, f.mu_dn = float(beta), float(mu_up), float(mu_dn)
+    for r in range(2):
+        for c in range(2):
+            f.U_re[r][c] = float(U[r, c].real)
+            f.U_im[r][c] = float(U[r, c].imag)
+    return f
+
+
+def _arg(x, shape):
+    """(pointer, on_device, keepalive) for a numpy array or a CUDA torch tensor of the given shape."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.shape != tuple(shape):
+            raise ValueError(f"expected C-contiguous float64 array of shape {tuple(shape)}, got {x.dtype} {x.shape}")
+        return x.ctypes.data, 0, x
+    try:
+        import torch
+    except ImportError as e:  # pragma: no cover
+        raise TypeError("expected numpy array") from e
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous() or tuple(x.shape) != tuple(shape):
+            raise ValueError(f"expected contiguous float64 tensor of shape {tuple(shape)}")
+        return x.data_ptr(), 1 if x.is_cuda else 0, x
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+class Solver:
+    """One simulation on one GPU (see include/qbe.h for the semantics of each call)."""
+
+    def __init__(self, N, Nx, J=32, M=32, L=12.0, R=7.5, device=0, stream=None):
+        self.N, self.Nx, self.J, self.M, self.L, self.R = N, Nx, J, M, L, R
+        g = QbeGrid(N, Nx, J, M, L, R, 0, device)
+        h = _c_void_p()
+        rc = lib().qbe_create(ctypes.byref(g), ctypes.byref(h))
+        if rc != 0:
+            raise QbeError(f"qbe_create failed with code {rc}")
+        self._h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = lib().qbe_last_error(self._h)
+            raise QbeError(f"{what} failed ({rc}): {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().qbe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: an int handle or a torch.cuda.Stream."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(lib().qbe_set_stream(self._h, _c_void_p(int(handle) if handle else 0)), "qbe_set_stream")
+
+    @property
+    def state_shape(self):
+        return (self.Nx, 4, self.N, self.N)
+
+    # -- configuration ----------------------------------------------------
+    def set_boundary(self, kind="periodic", left=None, right=None, alpha=0.0):
+        k = _BC[kind] if isinstance(kind, str) else int(kind)
+        lp = ctypes.byref(left) if left is not None else None
+        rp = ctypes.byref(right) if right is not None else None
+        self._check(lib().qbe_set_boundary(self._h, k, lp, rp, float(alpha)), "qbe_set_boundary")
+
+    def set_bfield(self, B):
+        p, dev, keep = _arg(B, (self.Nx, 3))
+        self._check(lib().qbe_set_bfield(self._h, _c_void_p(p), dev), "qbe_set_bfield")
+
+    def set_state(self, w):
+        p, dev, keep = _arg(w, self.state_shape)
+        self._check(lib().qbe_set_state(self._h, _c_void_p(p), dev), "qbe_set_state")
+
+    def get_state(self, out=None):
+        out = np.empty(self.state_shape) if out is None else out
+        p, dev, keep = _arg(out, self.state_shape)
+        self._check(lib().qbe_get_state(self._h, _c_void_p(p), dev), "qbe_get_state")
+        return out
+
+    # -- the hot path -----------------------------------------------------
+    def collide(self, w, out=None):
+        """C[W] for w[ncells][4][N][N] (host numpy or CUDA tensor); result in the same memory kind."""
+        ncells = w.shape[0]
+        shape = (ncells, 4, self.N, self.N)
+        pw, dev, keep = _arg(w, shape)
+        if out is None:
+            if dev:
+                import torch
+                out = torch.empty(shape, dtype=torch.float64, device=w.device)
+            else:
+                out = np.empty(shape)
+        po, dev2, keep2 = _arg(out, shape)
+        if dev2 != dev:
+            raise ValueError("input and output must both be host or both be device memory")
+        self._check(lib().qbe_collide(self._h, _c_void_p(pw), _c_void_p(po), ncells, dev), "qbe_collide")
+        return out
+
+    def advect(self, tau):
+        self._check(lib().qbe_advect(self._h, float(tau)), "qbe_advect")
+
+    def collide_rk2(self, dt):
+        self._check(lib().qbe_collide_rk2(self._h, float(dt)), "qbe_collide_rk2")
+
+    def step(self, dt, nsteps=1):
+        self._check(lib().qbe_step(self._h, float(dt), int(nsteps)), "qbe_step")
+
+    def moments(self):
+        rho = np.empty((self.Nx, 4))
+        mom = np.empty((self.Nx, 2))
+        en = np.empty(self.Nx)
+        self._check(lib().qbe_moments(self._h, _c_void_p(rho.ctypes.data), _c_void_p(mom.ctypes.data),
+                                      _c_void_p(en.ctypes.data), 0), "qbe_moments")
+        return rho, mom, en
+
+    def launch_count(self):
+        return int(lib().qbe_launch_count(self._h))
+
+    def enable_timing(self, on=True):
+        self._check(lib().qbe_enable_timing(self._h, 1 if on else 0), "qbe_enable_timing")
+
+    def kernel_time(self, group):
+        """(total device ms, launches) of a kernel group since enable_timing()."""
+        ms, n = _c_double(), ctypes.c_longlong()
+        self._check(lib().qbe_kernel_time(self._h, KERNEL_GROUPS[group], ctypes.byref(ms), ctypes.byref(n)),
+                    "qbe_kernel_time")
+        return ms.value, n.value

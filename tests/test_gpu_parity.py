@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (FP64 on both sides; the two evaluate the same discrete operator
+with different summation orders):
+* C[W]: max |C_gpu - C_oracle| <= 1e-11 * max |C_oracle| per evaluation.  The
+  operator is a sum of about 36 J M + 16 J fine-grid FFT convolutions, each
+  with a relative rounding error of order eps * log2(n^2) ~ 3e-15, summed over
+  J M ~ 1e3 terms whose magnitudes are up to ~10 times |C| (gain and loss
+  cancel), which bounds the difference by about 1e-12 relative; 1e-11 leaves
+  a factor of ten.
+* transport alone: 1e-13 (a handful of flops per value).
+* time steps: the collision bound above, carried through the RK2 update.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import qbe_oracle as O
+from paper_1408_1782_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_C = 1e-11
+TOL_ADV = 1e-13
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def qbe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1408_1782_gb300 import qbe as q
+
+    return q
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def gpu_collide(q, w, N, J, M, nb=None):
+    import torch
+
+    s = q.Solver(N, nb or w.shape[0], J=J, M=M, stream=torch.cuda.current_stream())
+    c = s.collide(torch.from_numpy(np.ascontiguousarray(w)).cuda())
+    torch.cuda.synchronize()
+    out = c.cpu().numpy()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("N,J,M,ncells", [(8, 4, 3, 5), (16, 8, 6, 3), (16, 32, 32, 2), (32, 8, 4, 2), (32, 6, 32, 1)])
+def test_collision_matches_oracle(qbe, N, J, M, ncells):
+    w = inputs.synthetic_w(N, ncells, seed=N + J + M)
+    got = gpu_collide(qbe, w, N, J, M)
+    ref = O.collision(w, O.Params(N=N, J=J, M=M))
+    for c in range(ncells):
+        assert rel(got[c], ref[c]) < TOL_C, (c, rel(got[c], ref[c]))
+
+
+def test_collision_large_grid_matches_oracle(qbe):
+    """N = 64 (the 128 x 128 padded grid of the benchmark workload), reduced quadrature."""
+    w = inputs.synthetic_w(64, 1, seed=5, perturb=0.05)
+    got = gpu_collide(qbe, w, 64, 4, 4)
+    ref = O.collision(w, O.Params(N=64, J=4, M=4))
+    assert rel(got, ref) < TOL_C
+
+
+def test_collision_host_and_device_paths_agree_and_batches_split(qbe):
+    """ncells larger than the solver's batch (ragged last batch), host and device memory."""
+    import torch
+
+    N, J, M = 16, 4, 4
+    w = inputs.synthetic_w(N, 5, seed=11)
+    s = qbe.Solver(N, 2, J=J, M=M, stream=torch.cuda.current_stream())
+    host = s.collide(w)
+    dev = s.collide(torch.from_numpy(w).cuda()).cpu().numpy()
+    assert np.array_equal(host, dev)
+    ref = O.collision(w, O.Params(N=N, J=J, M=M))
+    assert rel(host, ref) < TOL_C
+    s.close()
+
+
+def test_collision_degenerate_states(qbe):
+    """W = 0 gives C = 0; W = 1/2 + a.sigma constant in v gives C = 0 (all terms cancel);
+    commuting states have no conservative part (checked through the oracle's split)."""
+    N, J, M = 16, 8, 4
+    w = np.zeros((2, 4, N, N))
+    w[1, 0] = 0.5
+    w[1, 1:] = np.array([0.1, -0.2, 0.05])[:, None, None]
+    got = gpu_collide(qbe, w, N, J, M)
+    assert np.abs(got[0]).max() == 0.0
+    assert np.abs(got[1]).max() < 1e-10
+    n = inputs.synthetic_w(N, 1, seed=3)[0, 0]
+    ws = np.zeros((1, 4, N, N))
+    ws[0, 0] = n
+    ws[0, 3] = 0.3 * n
+    got = gpu_collide(qbe, ws, N, J, M)
+    ref = O.collision(ws, O.Params(N=N, J=J, M=M))
+    assert rel(got, ref) < TOL_C
+    assert np.abs(got[0, 1:3]).max() < 1e-12 * np.abs(got).max()
+
+
+def test_collision_conserves_density_like_the_oracle(qbe):
+    N, J, M = 16, 32, 32
+    w = inputs.synthetic_w(N, 2, seed=1)
+    got = gpu_collide(qbe, w, N, J, M)
+    p = O.Params(N=N, J=J, M=M)
+    rho, _, _ = O.moments(got, p)
+    scale = O.delta_v(p) ** 2 * np.abs(got).sum(axis=(1, 2, 3))
+    assert np.all(np.abs(rho).max(axis=1) < 1e-13 * scale)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet", "maxwell"])
+def test_transport_matches_oracle(qbe, bc):
+    import torch
+
+    N, Nx = 8, 7
+    rng = np.random.default_rng(4)
+    W = inputs.synthetic_w(N, Nx, seed=2) + 0.01 * rng.normal(size=(Nx, 4, N, N))
+    fdL = (0.8, 1.5, -1.5, np.eye(2))
+    fdR = (1.2, 1.5, -1.5, np.array([[1, -1], [1, 1]]) / np.sqrt(2))
+    obc = O.Boundary(bc, fdL, fdR, alpha=0.4)
+    s = qbe.Solver(N, Nx, J=2, M=1, stream=torch.cuda.current_stream())
+    if bc != "periodic":
+        s.set_boundary(bc, qbe.fd_state(*fdL), qbe.fd_state(*fdR), alpha=0.4)
+    s.set_state(W)
+    tau = 2.6 / Nx / 12.0                    # |nu| = 2.6 -> three sub-steps
+    s.advect(tau)
+    got = s.get_state()
+    ref = O.advect(W, tau, O.Params(N=N), obc)
+    assert rel(got, ref) < TOL_ADV
+    s.close()
+
+
+def test_rk2_substep_with_field_matches_oracle(qbe):
+    import torch
+
+    N, Nx, J, M = 8, 3, 4, 4
+    W = inputs.synthetic_w(N, Nx, seed=6)
+    B = inputs.rotating_b(Nx)
+    s = qbe.Solver(N, Nx, J=J, M=M, stream=torch.cuda.current_stream())
+    s.set_state(W)
+    s.set_bfield(B)
+    s.collide_rk2(0.003)
+    got = s.get_state()
+    ref = O.collide_rk2(W, B, 0.003, O.Params(N=N, J=J, M=M))
+    assert rel(got - W, ref - W) < 1e-10
+    assert rel(got, ref) < TOL_C
+    s.close()
+
+
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet", "maxwell"])
+def test_split_steps_match_oracle(qbe, bc):
+    import torch
+
+    N, Nx, J, M = 16, 5, 4, 4
+    W = inputs.synthetic_w(N, Nx, seed=8, perturb=0.05)
+    B = inputs.uniform_b(Nx, (0.3, 0.0, 0.4))
+    fd = (1.0, 0.0, 0.0, np.eye(2))
+    obc = O.Boundary(bc, fd, fd, alpha=0.5)
+    p = O.Params(N=N, J=J, M=M)
+    s = qbe.Solver(N, Nx, J=J, M=M, stream=torch.cuda.current_stream())
+    if bc != "periodic":
+        s.set_boundary(bc, qbe.fd_state(*fd), qbe.fd_state(*fd), alpha=0.5)
+    s.set_state(W)
+    s.set_bfield(B)
+    s.step(0.004, 2)
+    got = s.get_state()
+    ref = W
+    for _ in range(2):
+        ref = O.step(ref, B, 0.004, p, obc)
+    assert rel(got, ref) < TOL_C
+    rho, mom, en = s.moments()
+    r2, m2, e2 = O.moments(ref, p)
+    assert rel(rho, r2) < 1e-12 and rel(mom, m2) < 1e-10 and rel(en, e2) < 1e-12
+    s.close()
+
+
+def test_api_errors_are_reported(qbe):
+    s = qbe.Solver(8, 2, J=2, M=1)
+    with pytest.raises(qbe.QbeError):
+        s.step(0.01, 1)                 # no state yet
+    with pytest.raises(qbe.QbeError):
+        s.set_boundary("maxwell", qbe.fd_state(1, 0, 0), qbe.fd_state(1, 0, 0), alpha=1.5)
+    with pytest.raises(qbe.QbeError):
+        s.set_boundary("dirichlet", qbe.fd_state(-1, 0, 0), qbe.fd_state(1, 0, 0))
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# Paper-parameter workloads against stored oracle results (tests/golden)
+# ---------------------------------------------------------------------------
+
+def test_plain_fp64_n16_ten_steps_match_stored_oracle(qbe):
+    """N=16, Nx=16 periodic, J=M=32, 10 split steps of dt=0.01 (the small plain-FP64 workload)."""
+    import torch
+
+    path = os.path.join(GOLDEN, "plain_fp64_n16.npz")
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    g = np.load(path)
+    wl = inputs.WORKLOADS["plain_fp64_n16"]
+    W0 = inputs.synthetic_w(wl["N"], wl["Nx"], L=wl["L"], seed=0)
+    assert rel(W0, g["W0"]) < 1e-13
+    s = qbe.Solver(wl["N"], wl["Nx"], J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"],
+                   stream=torch.cuda.current_stream())
+    s.set_state(g["W0"])
+    s.set_bfield(inputs.uniform_b(wl["Nx"], wl["B"]))
+    s.step(wl["dt"], 1)
+    assert rel(s.get_state(), g["W1"]) < TOL_C
+    s.step(wl["dt"], wl["steps"] - 1)
+    W10 = s.get_state()
+    assert rel(W10, g["W10"]) < 10 * TOL_C
+    rho, mom, en = s.moments()
+    assert rel(rho, g["rho"][-1]) < 1e-11 and rel(en, g["energy"][-1]) < 1e-11
+    # total density conserved to round-off by transport (periodic) and to the quadrature level by C
+    rho0 = O.moments(g["W0"], O.Params(N=16))[0].sum(0)
+    assert np.abs(rho.sum(0) - rho0).max() < 1e-12 * np.abs(rho0).max()
+    s.close()
+
+
+def test_plain_fp64_n64_sampled_cells_match_stored_oracle(qbe):
+    """N=64, Nx=128 Dirichlet workload at full size: C[W] of all 128 cells in the benchmark's launch
+    configuration; two sampled cells compared with the oracle, the rest checked for finiteness and
+    density conservation."""
+    import torch
+
+    path = os.path.join(GOLDEN, "plain_fp64_n64_cells.npz")
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    g = np.load(path)
+    wl = inputs.WORKLOADS["plain_fp64_n64"]
+    W = inputs.synthetic_w(wl["N"], wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])
+    cells = g["cells"]
+    assert rel(W[cells], g["W"]) < 1e-12
+    W[cells] = g["W"]
+    got = gpu_collide(qbe, W, wl["N"], wl["J"], wl["M"])
+    for i, c in enumerate(cells):
+        assert rel(got[c], g["C"][i]) < TOL_C
+    assert np.isfinite(got).all()
+    p = O.Params(N=64)
+    rho, _, _ = O.moments(got, p)
+    scale = O.delta_v(p) ** 2 * np.abs(got).sum(axis=(1, 2, 3))
+    assert np.all(np.abs(rho).max(axis=1) < 1e-10 * scale)
