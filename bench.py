@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the split time step (transport + RK2[C + precession] + transport).
+
+Default workload (plain FP64 at scale): N = 64 velocity points per dimension,
+Nx = 128 cells, Dirichlet walls (Fermi-Dirac beta = 1, mu = 0, U = 1),
+B = (0, 0, 0.5), dt = 0.005, J = M = 32, L = 12, R = 7.5, seeded synthetic
+Fermi-Dirac-perturbed state (5 % Hermitian perturbation).  One step = one
+split time step of all 128 cells = 2 collision-operator evaluations.
+
+Prints one JSON line (rank 0).  Metric: C[W] cell*k-pts/s
+(= 2 * Nx * N^2 collision evaluations per step / time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --mode collide [--cells C]   # time C[W] alone on the first C cells
+
+--mode collide (not the benchmark line; used for profiling) times only the
+collision operator, one evaluation of the first C cells per step.
+
+--impl reference times the FP64 CPU oracle (the baseline: no other
+implementation of this method exists) on the host cores, one cell's C[W] per
+step, on the same workload.  Under torchrun with N > 1, "ours" runs independent
+replicas (one full simulation per GPU, weak scaling); "reference" runs on rank 0
+only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (profiles/fp64_fp32_issue_rates.md)
+
+
+def workload():
+    from paper_1408_1782_gb300 import inputs
+    return dict(inputs.WORKLOADS["plain_fp64_n64"])
+
+
+def i3_flops_per_unit(N):
+    """Algorithmic FLOPs of one (cell, j, m) unit of the I3 (Hu-Ying) term, FFT convention:
+    36 real 2-D transforms of P = (2N)^2 points at 2.5 P log2 P each (4 shifts, 16 forward,
+    16 inverse) plus 67 P pointwise flops (16 products, 16 psi' scalings of complex spectra,
+    16 multiply-adds, the shift phases)."""
+    P = (2 * N) ** 2
+    return 90.0 * P * math.log2(P) + 67.0 * P
+
+
+# ---------------------------------------------------------------------------
+# CPU side (the oracle): a bounded sample on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, ncores, repeats=1, warmup=0):
+    """Time the oracle's C[W] for one cell of the workload (its 60 independent integral
+    terms spread over `ncores` spawned processes).  Returns (seconds per sample, cores)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from oracle import qbe_oracle as O
+    from paper_1408_1782_gb300 import inputs
+
+    p = O.Params(N=wl["N"], L=wl["L"], R=wl["R"], J=wl["J"], M=wl["M"])
+    W = inputs.synthetic_w(wl["N"], wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])
+    cell = np.ascontiguousarray(W[:1])
+    ctx = mp.get_context("spawn")
+    times = []
+    with ctx.Pool(ncores) as pool:
+        mapper = lambda f, it: pool.map(f, list(it), chunksize=1)
+        small = O.Params(N=8, J=2, M=1)
+        for _ in range(warmup):                           # untimed; numpy has nothing to warm up
+            O.collision(inputs.synthetic_w(8, 1, seed=1), small, mapper=mapper)
+        for _ in range(repeats):
+            t = time.perf_counter()
+            O.collision(cell, p, mapper=mapper)
+            times.append(time.perf_counter() - t)
+    return times, ncores
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workload()
+    ncores = min(16, host_cores())
+    times, cores = oracle_sample(wl, ncores, repeats=args.steps, warmup=args.warmup)
+    T = sum(times)
+    npts = wl["N"] ** 2
+    value = args.steps * npts / T
+    sample = (f"per step: C[W] of 1 of the {wl['Nx']} cells (N={wl['N']}, J=M={wl['J']}), the oracle's "
+              f"60 integral terms on {cores} spawned processes")
+    line = {
+        "impl": "reference", "metric": "C[W] cell·k-pts/s", "value": value, "unit": "cell·k-pts/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Fermi-Dirac-perturbed W)",
+        "config": config_dict(wl, args.gpus, reference=True),
+        "cpu_baseline": {"value": value, "unit": "cell·k-pts/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell·k-pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(wl, ngpu, reference=False):
+    return {
+        "workload": (f"plain FP64 at scale: {wl['N']}x{wl['N']} velocity grid, Nx={wl['Nx']} cells, "
+                     f"Dirichlet walls (Fermi-Dirac beta=1, mu=0), B=(0,0,0.5), dt={wl['dt']}, "
+                     f"J=M={wl['J']}, L={wl['L']}, R={wl['R']}, 5% perturbed synthetic W"),
+        "N": wl["N"], "Nx": wl["Nx"], "J": wl["J"], "M": wl["M"], "dt": wl["dt"],
+        "bc": "dirichlet", "B": list(wl["B"]),
+        "l2": "256 MiB buffer zeroed before every timed step (working set also exceeds L2)",
+        "parallelism": "oracle on host cores" if reference else ("single GPU" if ngpu == 1 else f"{ngpu} replicas"),
+    }
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_sel):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.sel = device_sel
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.sel is not None:
+            cmd += ["-i", str(self.sel)]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1408_1782_gb300 import decomp, inputs, qbe
+
+    wl = workload()
+    if args.mode == "collide":
+        return run_collide_only(args, wl, local)
+    N, Nx = wl["N"], wl["Nx"]
+    stream = torch.cuda.current_stream()
+    s = qbe.Solver(N, Nx, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream)
+    fd = qbe.fd_state(wl["wall"]["beta"], wl["wall"]["mu_up"], wl["wall"]["mu_dn"])
+    s.set_boundary("dirichlet", fd, fd)
+    s.set_bfield(inputs.uniform_b(Nx, wl["B"]))
+    W0 = inputs.synthetic_w(N, Nx, L=wl["L"], seed=0, perturb=wl["perturb"])
+    s.set_state(W0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        s.step(wl["dt"], 1)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    s.enable_timing(True)
+    launches0 = s.launch_count()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        s.step(wl["dt"], 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = s.launch_count() - launches0
+    t_ms = decomp.max_over_ranks(e0.elapsed_time(e1))
+    groups = {}
+    for gname in qbe.KERNEL_GROUPS:
+        ms, cnt = s.kernel_time(gname)
+        groups[gname] = {"ms": ms, "launches": cnt}
+    s.enable_timing(False)
+
+    units_per_step = 2 * Nx * N * N
+    value = world * args.steps * units_per_step / (t_ms * 1e-3)
+
+    # end to end through host buffers: pinned host state in, step, state out
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    host = torch.from_numpy(W0).pin_memory()
+    host_out = torch.empty_like(host).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(host)            # H2D from pinned host memory inside the C call
+        s.step(wl["dt"], 1)
+        s.get_state(host_out)        # D2H of the step's result (synchronises)
+    t_e2e = decomp.max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * e2e_steps * units_per_step / t_e2e
+    state_bytes = W0.nbytes
+
+    # roofline of the dominant kernel (I3, Hu-Ying term): FP64 ALU bound
+    i3 = groups["i3"]
+    avg_i3_s = i3["ms"] * 1e-3 / max(i3["launches"], 1)
+    flops_per_launch = Nx * wl["J"] * wl["M"] * i3_flops_per_unit(N)
+    achieved = flops_per_launch / avg_i3_s / 1e12
+    sm_max = 2070.0
+    try:
+        sm_max = float(json.load(open(MEASURED_PEAKS)).get("sm_max_mhz", sm_max))
+    except Exception:
+        pass
+    peak = SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+    total_group_ms = sum(v["ms"] for v in groups.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ncores = min(16, host_cores())
+        times, cores = oracle_sample(wl, ncores, repeats=1)
+        cpu = {"value": N * N / times[0], "unit": "cell·k-pts/s", "cores": cores, "kind": "oracle",
+               "sample": (f"C[W] of 1 of the {Nx} cells (N={N}, J=M={wl['J']}): the oracle's 60 integral "
+                          f"terms on {cores} spawned processes, {times[0]:.1f} s")}
+
+    if rank == 0:
+        line = {
+            "metric": "C[W] cell·k-pts/s", "value": value, "unit": "cell·k-pts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "steps_per_s": 1e3 * args.steps / t_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)",
+            "config": config_dict(wl, world),
+            "roofline": {"kernel": "k_i3 (Hu-Ying I3 term)", "bound": "alu", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_i3_s * 1e3,
+                         "peak_source": (f"derived: {SM_COUNT} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x 2 "
+                                         f"flop x {sm_max:.0f} MHz (DFMA microbenchmark 1.20 TFLOP/s at 2002 MHz)")},
+            "kernel_share": {k: round(v["ms"] / total_group_ms, 4) for k, v in groups.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "cell·k-pts/s", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_collide_only(args, wl, local):
+    """C[W] evaluations of the first `cells` cells of the workload's initial state."""
+    import torch
+
+    from paper_1408_1782_gb300 import inputs, qbe
+
+    N = wl["N"]
+    cells = args.cells or wl["Nx"]
+    stream = torch.cuda.current_stream()
+    s = qbe.Solver(N, cells, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream)
+    W = inputs.synthetic_w(N, wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])[:cells]
+    w = torch.from_numpy(W.copy()).cuda()
+    c = torch.empty_like(w)
+    for _ in range(args.warmup):
+        s.collide(w, c)
+    torch.cuda.synchronize()
+    s.enable_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.collide(w, c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    i3_ms, i3_n = s.kernel_time("i3")
+    flops = cells * wl["J"] * wl["M"] * i3_flops_per_unit(N)
+    line = {"mode": "collide", "metric": "C[W] cell·k-pts/s", "value": args.steps * cells * N * N / (t_ms * 1e-3),
+            "unit": "cell·k-pts/s", "cells": cells, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_eval": t_ms / args.steps, "i3_ms_per_launch": i3_ms / max(i3_n, 1),
+            "i3_tflops": flops / (i3_ms / max(i3_n, 1) * 1e-3) / 1e12, "dtype": "f64"}
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["step", "collide"], default="step")
+    ap.add_argument("--cells", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

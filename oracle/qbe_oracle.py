@@ -298,42 +298,72 @@ def I3(fh, gh, hh, p: Params):
 # (eq. CcPauliCarleman and the Carleman form of eq. CdPauli, Sec. 3.1-3.2)
 # ----------------------------------------------------------------------------
 
-def collision_xi(wh: np.ndarray, p: Params):
-    """C[W] on Xi from embedded Pauli coefficients wh [..., 4, 2N, 2N]; returns (Cc_hat, Cd_hat)."""
+def collision_terms(wh: np.ndarray, p: Params):
+    """The Pauli-form collision operator as a list of integral terms.
+
+    Each entry (part, component, coefficient, kind, f, g, h) contributes
+    coefficient * I_kind[f, g, h] to component `component` of C_c (part "c") or
+    C_d (part "d"); wh [..., 4, 2N, 2N] are embedded Pauli coefficients.
+    """
     N = p.N
     one = np.zeros(wh.shape[:-3] + (2 * N, 2 * N), dtype=np.complex128)
     one[..., N, N] = 1.0                                       # the constant function 1
     w = [wh[..., a, :, :] for a in range(4)]
     ew = [ETA[a] * w[a] for a in range(4)]                      # (eta w)_a
     f = 2.0 * w[0] - one                                       # 2 w0 - 1
-    Cc = np.zeros_like(wh)
-    Cd = np.zeros_like(wh)
+    terms = []
     # Conservative part: i (2w0(v+u) - 1) [W(v+u+u'), W(v)] with -i[W2, W1] = 2 (w2 x w1).sigma
     for (c, d, e, s) in LEVI_CIVITA:
-        Cc[..., c, :, :] += -2.0 * s * I1(f, w[d], w[e], p)
+        terms.append(("c", c, -2.0 * s, "I1", f, w[d], w[e]))
     # Dissipative part, first term: 2 pi <w(v+u), w(v+u')>_eta (1 - W(v))
     for c in range(4):
-        h = (one if c == 0 else 0.0) - w[c]
+        h = (one if c == 0 else 0.0 * one) - w[c]
         for a in range(4):
-            Cd[..., c, :, :] += 2.0 * np.pi * ETA[a] * I2(w[a], w[a], h, p)
+            terms.append(("d", c, 2.0 * np.pi * ETA[a], "I2", w[a], w[a], h))
     # second term: -2 pi <w(v+u), w(v+u')>_eta (eta w(v+u+u')).sigma
     for c in range(4):
         for a in range(4):
-            Cd[..., c, :, :] += -2.0 * np.pi * ETA[a] * I3(w[a], w[a], ew[c], p)
+            terms.append(("d", c, -2.0 * np.pi * ETA[a], "I3", w[a], w[a], ew[c]))
     # third term: pi (2 w0(v+u) - 1) {W(v), (eta w(v+u+u')).sigma}, with
     # {W1, W2} = 2((w1_0 w2 + w2_0 w1).sigma - <w1, w2>_eta 1)
-    Cd[..., 0, :, :] += 2.0 * np.pi * (2.0 * I4(f, ew[0], w[0], p))
+    terms.append(("d", 0, 4.0 * np.pi, "I4", f, ew[0], w[0]))
     for a in range(4):
-        Cd[..., 0, :, :] += -2.0 * np.pi * ETA[a] * I4(f, ew[a], w[a], p)
+        terms.append(("d", 0, -2.0 * np.pi * ETA[a], "I4", f, ew[a], w[a]))
     for c in range(1, 4):
-        Cd[..., c, :, :] += 2.0 * np.pi * (I4(f, ew[c], w[0], p) + I4(f, ew[0], w[c], p))
+        terms.append(("d", c, 2.0 * np.pi, "I4", f, ew[c], w[0]))
+        terms.append(("d", c, 2.0 * np.pi, "I4", f, ew[0], w[c]))
+    return terms
+
+
+_INTEGRALS = {"I1": I1, "I2": I2, "I3": I3, "I4": I4}
+
+
+def evaluate_term(args):
+    """Evaluate one (kind, f, g, h, params) integral term (usable with any map)."""
+    kind, f, g, h, p = args
+    return _INTEGRALS[kind](f, g, h, p)
+
+
+def collision_xi(wh: np.ndarray, p: Params, mapper=map):
+    """C[W] on Xi from embedded Pauli coefficients wh [..., 4, 2N, 2N]; returns (Cc_hat, Cd_hat).
+
+    The terms are independent; `mapper` (default: the builtin map) may evaluate
+    them concurrently.  They are summed in list order.
+    """
+    terms = collision_terms(wh, p)
+    values = list(mapper(evaluate_term, [(t[3], t[4], t[5], t[6], p) for t in terms]))
+    Cc = np.zeros_like(wh)
+    Cd = np.zeros_like(wh)
+    for (part, c, coef, _kind, _f, _g, _h), v in zip(terms, values):
+        tgt = Cc if part == "c" else Cd
+        tgt[..., c, :, :] += coef * v
     return Cc, Cd
 
 
-def collision_parts(w: np.ndarray, p: Params):
+def collision_parts(w: np.ndarray, p: Params, mapper=map):
     """(C_c, C_d) on the velocity grid for Pauli states w [..., 4, N, N] (real)."""
     wh = embed(coarse_to_xi(w.astype(np.complex128), p), p)
-    Cc_h, Cd_h = collision_xi(wh, p)
+    Cc_h, Cd_h = collision_xi(wh, p, mapper)
     out = []
     for Ch in (Cc_h, Cd_h):
         cx = restrict(Ch, p).copy()
@@ -344,9 +374,9 @@ def collision_parts(w: np.ndarray, p: Params):
     return out[0], out[1]
 
 
-def collision(w: np.ndarray, p: Params, return_imag: bool = False):
+def collision(w: np.ndarray, p: Params, return_imag: bool = False, mapper=map):
     """C[W] = C_c + C_d on the grid (real part; imaginary residue optionally returned)."""
-    Cc, Cd = collision_parts(w, p)
+    Cc, Cd = collision_parts(w, p, mapper)
     C = Cc + Cd
     if return_imag:
         return C.real.copy(), C.imag.copy()
@@ -461,21 +491,25 @@ def _ghosts(W, p: Params, bc: Boundary):
     raise ValueError(bc.kind)
 
 
-def advect_substep(W, tau, dx, p: Params, bc: Boundary):
-    """One application of eq. slopeLimiterStep with time step tau (Delta t -> tau)."""
+def limiter_update(ext, tau, dx, p: Params):
+    """eq. slopeLimiterStep (Delta t -> tau) on the interior of ext [n+4, 4, N, N] (two ghosts per side)."""
     vx, _ = velocity_nodes(p)
-    Nx = W.shape[0]
-    ext = _ghosts(W, p, bc)
-    # S_j for j = -1 .. Nx (ext indices 1 .. Nx+2)
+    n = ext.shape[0] - 4
+    # S_j for j = -1 .. n (ext indices 1 .. n+2)
     S = np.zeros_like(ext)
-    S[1:Nx + 3] = minmod(ext[2:Nx + 4] - ext[1:Nx + 3], ext[1:Nx + 3] - ext[0:Nx + 2])
+    S[1:n + 3] = minmod(ext[2:n + 4] - ext[1:n + 3], ext[1:n + 3] - ext[0:n + 2])
     nu = tau * vx / dx
     lim = 0.5 * (np.sign(nu) - nu)
-    Wm1, W0, Wp1 = ext[1:Nx + 1], ext[2:Nx + 2], ext[3:Nx + 3]
-    Sm1, S0, Sp1 = S[1:Nx + 1], S[2:Nx + 2], S[3:Nx + 3]
+    Wm1, W0, Wp1 = ext[1:n + 1], ext[2:n + 2], ext[3:n + 3]
+    Sm1, S0, Sp1 = S[1:n + 1], S[2:n + 2], S[3:n + 3]
     godunov = -vx * (Wp1 - Wm1) + np.abs(vx) * (Wp1 - 2.0 * W0 + Wm1)
     limiter = lim * (-vx * (Sp1 - Sm1) + np.abs(vx) * (Sp1 - 2.0 * S0 + Sm1))
     return W0 + (tau / (2.0 * dx)) * (godunov + limiter)
+
+
+def advect_substep(W, tau, dx, p: Params, bc: Boundary):
+    """One application of eq. slopeLimiterStep with time step tau (Delta t -> tau)."""
+    return limiter_update(_ghosts(W, p, bc), tau, dx, p)
 
 
 def transport_substeps(tau, dx, p: Params, nu_max: float = 1.0) -> int:

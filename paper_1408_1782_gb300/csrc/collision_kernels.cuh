@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_i24(const double2* what, const dou
 // written to its own slot of K3part and reduced in fixed order later.
 // --------------------------------------------------------------------------
 template <int n>
-__global__ void __launch_bounds__(kThreads) k_i3(const double2* what, const double2* wfine, double2* K3part,
+__global__ void __launch_bounds__(kThreads, 3) k_i3(const double2* what, const double2* wfine, double2* K3part,
                                                  double2* ws, const double2* __restrict__ gtw,
                                                  const double* __restrict__ psip_s,
                                                  const double2* __restrict__ phase, int J, int M, int nmc, int mch,
@@ -231,6 +231,17 @@ __global__ void __launch_bounds__(kThreads) k_i3(const double2* what, const doub
   extern __shared__ double2 smem[];
   double2* tw = smem;
   double2* sm = smem + n;
+  __shared__ int xcols[n];          // permuted positions whose frequency lies in Xi (incl. its -N/2 line)
+  __shared__ unsigned char xmask[n];
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int pos = 0; pos < n; ++pos) {
+      const int k = freq_of_pos<n>(pos);
+      const bool in = (k < n / 4) || (k >= n - n / 4);
+      xmask[pos] = in ? 1 : 0;
+      if (in) xcols[c++] = pos;
+    }
+  }
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
   double2* slot = ws + (size_t)blockIdx.x * 3 * P;
@@ -251,11 +262,15 @@ __global__ void __launch_bounds__(kThreads) k_i3(const double2* what, const doub
       for (int p = 0; p < 2; ++p) {
         const double2* in = what + ((size_t)c * 4 + p) * P;
         double2* S = Sig + (size_t)p * P;
-        col_pass<n, 1, false, 0>(
-            sm, tw, [&](int ix, int iy) { return cmul(in[ix * n + iy], cmul(px[ix], py[iy])); }, NoMid(),
-            [&](int ix, int iy, double2 v) { S[ix * n + iy] = v; });
+        // only the n/2 columns (y frequencies) of Xi are non-zero: transform those
+        col_pass_list<n, 1, false, 0>(
+            sm, tw, xcols, n / 2,
+            [&](int ix, int iy) {
+              return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : make_double2(0.0, 0.0);
+            },
+            NoMid(), [&](int ix, int iy, double2 v) { S[ix * n + iy] = v; });
         row_pass<n, 1, false, 0>(
-            sm, tw, [&](int ix, int iy) { return S[ix * n + iy]; }, NoMid(),
+            sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : make_double2(0.0, 0.0); }, NoMid(),
             [&](int ix, int iy, double2 v) { S[ix * n + iy] = v; });
       }
       for (int a = 0; a < 4; ++a) {
@@ -273,9 +288,9 @@ __global__ void __launch_bounds__(kThreads) k_i3(const double2* what, const doub
                 return cscale(Sp[ix * n + iy], im ? z.y : z.x);
               },
               NoMid(), [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
-          col_pass<n, -1, true, 1>(
+          col_conv_pass<n>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
-              [&](int ix, int iy, double2 v) { return cscale(v, psp[ix * n + iy]); },
+              [&](int ix, int iy) { return psp[ix * n + iy]; },
               [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
           row_pass<n, 1, false, 0>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
@@ -381,7 +396,21 @@ size_t smem_bytes() {
 }
 
 template <int n>
+void set_smem_attributes() {
+  static bool done = false;
+  if (done) return;
+  const int sm = (int)smem_bytes<n>();
+  cudaFuncSetAttribute(k_prep<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i1<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i24<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i3<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_assemble<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  done = true;
+}
+
+template <int n>
 int i3_blocks_per_sm() {
+  set_smem_attributes<n>();
   int b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n>, kThreads, smem_bytes<n>());
   return b < 1 ? 1 : b;
@@ -390,6 +419,7 @@ int i3_blocks_per_sm() {
 template <int n>
 cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells,
                             cudaStream_t s, long long& launches, KernelTimer* tm) {
+  set_smem_attributes<n>();
   const size_t sm = smem_bytes<n>();
   auto begin = [&](int g) { if (tm) tm->begin(g, s); };
   auto end = [&]() { if (tm) tm->end(s); };

@@ -80,6 +80,9 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
 }
 
 // One radix-2 decimation-in-time stage of butterfly span S on R registers.
+// Butterflies with a non-trivial twiddle w = c + i s use the cosine-factored
+// form (u +- w x) = u +- c (x + (s/c) i x): six FMAs instead of two products,
+// two FMAs and four additions (|s/c| <= tan(3 pi/8) for R <= 16).
 template <int R, int SIGN, int S>
 struct DftStage {
   __device__ __forceinline__ static void run(double2 (&b)[R]) {
@@ -87,10 +90,21 @@ struct DftStage {
     for (int g = 0; g < R; g += S) {
 #pragma unroll
       for (int k = 0; k < S / 2; ++k) {
-        const double2 t = twid<16, SIGN>(k * (16 / S), b[g + k + S / 2]);
+        const int k16 = (k * (16 / S)) & 15;
         const double2 u = b[g + k];
-        b[g + k] = cadd(u, t);
-        b[g + k + S / 2] = csub(u, t);
+        const double2 x = b[g + k + S / 2];
+        if ((k16 & 3) == 0) {
+          const double2 t = twid<16, SIGN>(k16, x);
+          b[g + k] = cadd(u, t);
+          b[g + k + S / 2] = csub(u, t);
+        } else {
+          const double c = cos16(k16);
+          const double r = (SIGN * sin16(k16)) / c;
+          const double qx = fma(-r, x.y, x.x);
+          const double qy = fma(r, x.x, x.y);
+          b[g + k] = make_double2(fma(c, qx, u.x), fma(c, qy, u.y));
+          b[g + k + S / 2] = make_double2(fma(-c, qx, u.x), fma(-c, qy, u.y));
+        }
       }
     }
     DftStage<R, SIGN, 2 * S>::run(b);
@@ -174,10 +188,62 @@ __device__ __forceinline__ void fft_lines(double2* buf, int nl, int ls, int es, 
   }
 }
 
+// Circular convolution along lines: forward FFT, multiplication of each
+// spectral value by mul(line, pos) (pos = permuted position), inverse FFT.  The
+// second forward stage, the multiplication and the first inverse stage act on
+// the same B contiguous values, so they are fused in registers.
+template <int n, class MUL>
+__device__ __forceinline__ void fft_conv_lines(double2* buf, int nl, int ls, int es, const double2* __restrict__ tw,
+                                               MUL mul) {
+  constexpr int A = Split<n>::A, B = Split<n>::B;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int task = tid; task < nl * B; task += nt) {
+    const int l = task % nl, t2 = task / nl;
+    double2* base = buf + l * ls + t2 * es;
+    double2 a[A];
+#pragma unroll
+    for (int t1 = 0; t1 < A; ++t1) a[t1] = base[B * t1 * es];
+    dft<A, -1>(a);
+#pragma unroll
+    for (int k1 = 1; k1 < A; ++k1) a[k1] = cmul(a[k1], tw[t2 * A + k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) base[B * k1 * es] = a[k1];
+  }
+  __syncthreads();
+  for (int task = tid; task < nl * A; task += nt) {
+    const int l = task % nl, k1 = task / nl;
+    double2* base = buf + l * ls + B * k1 * es;
+    double2 b[B];
+#pragma unroll
+    for (int t2 = 0; t2 < B; ++t2) b[t2] = base[t2 * es];
+    dft<B, -1>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) b[k2] = cscale(b[k2], mul(l, B * k1 + k2));
+    dft<B, 1>(b);
+#pragma unroll
+    for (int t2 = 0; t2 < B; ++t2) base[t2 * es] = b[t2];
+  }
+  __syncthreads();
+  for (int task = tid; task < nl * B; task += nt) {
+    const int l = task % nl, t2 = task / nl;
+    double2* base = buf + l * ls + t2 * es;
+    double2 a[A];
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) a[k1] = base[B * k1 * es];
+#pragma unroll
+    for (int k1 = 1; k1 < A; ++k1) a[k1] = cmulc(a[k1], tw[t2 * A + k1]);
+    dft<A, 1>(a);
+#pragma unroll
+    for (int t1 = 0; t1 < A; ++t1) base[B * t1 * es] = a[t1];
+  }
+  __syncthreads();
+}
+
 // Chunk sizes (rows per row-pass chunk, columns per column-pass chunk) so that a
-// chunk of complex doubles occupies about 32 KB of shared memory.
+// chunk of complex doubles occupies about 64 KB of shared memory (three blocks
+// per SM fit) and the radix-B stage has at least one task per thread.
 template <int n> struct Chunk {
-  static constexpr int RC = (n >= 256) ? 8 : (n >= 128) ? 16 : (n >= 64) ? 32 : n;
+  static constexpr int RC = (n >= 256) ? 16 : (n >= 128) ? 32 : n;
   static constexpr int CC = RC;
   static constexpr int LS = n + 1;                 // padded row stride (odd => no bank conflicts)
   static constexpr int SMEM_ELEMS = (RC * LS > CC * n ? RC * LS : CC * n);
@@ -236,6 +302,57 @@ __device__ __forceinline__ void col_pass(double2* sm, const double2* tw, LD ld, 
     for (int idx = tid; idx < CC * n; idx += nt) {
       const int ix = idx / CC, c = idx % CC;
       st(ix, c0 + c, sm[ix * CC + c]);
+    }
+    __syncthreads();
+  }
+}
+
+// Column pass doing a circular convolution along ix for each column iy:
+// sm[ix][c] = ld(ix, iy); forward FFT; times mul(pos_x, iy); inverse FFT; st(ix, iy, value).
+template <int n, class LD, class MUL, class ST>
+__device__ __forceinline__ void col_conv_pass(double2* sm, const double2* tw, LD ld, MUL mul, ST st) {
+  constexpr int CC = Chunk<n>::CC;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c0 = 0; c0 < n; c0 += CC) {
+    for (int idx = tid; idx < CC * n; idx += nt) {
+      const int ix = idx / CC, c = idx % CC;
+      sm[ix * CC + c] = ld(ix, c0 + c);
+    }
+    __syncthreads();
+    fft_conv_lines<n>(sm, CC, 1, CC, tw, [&](int l, int pos) { return mul(pos, c0 + l); });
+    for (int idx = tid; idx < CC * n; idx += nt) {
+      const int ix = idx / CC, c = idx % CC;
+      st(ix, c0 + c, sm[ix * CC + c]);
+    }
+    __syncthreads();
+  }
+}
+
+// Column pass over a subset of columns cols[0..ncols) (chunks of CC columns).
+template <int n, int DIR1, bool HAS_MID, int DIR2, class LD, class MID, class ST>
+__device__ __forceinline__ void col_pass_list(double2* sm, const double2* tw, const int* cols, int ncols, LD ld,
+                                              MID mid, ST st) {
+  constexpr int CC = Chunk<n>::CC;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c0 = 0; c0 < ncols; c0 += CC) {
+    const int nc = (ncols - c0) < CC ? (ncols - c0) : CC;
+    for (int idx = tid; idx < nc * n; idx += nt) {
+      const int ix = idx / nc, c = idx % nc;
+      sm[ix * CC + c] = ld(ix, cols[c0 + c]);
+    }
+    __syncthreads();
+    if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1)>(sm, nc, 1, CC, tw);
+    if (HAS_MID) {
+      for (int idx = tid; idx < nc * n; idx += nt) {
+        const int ix = idx / nc, c = idx % nc;
+        sm[ix * CC + c] = mid(ix, cols[c0 + c], sm[ix * CC + c]);
+      }
+      __syncthreads();
+    }
+    if (DIR2 != 0) fft_lines<n, (DIR2 < 0 ? -1 : 1)>(sm, nc, 1, CC, tw);
+    for (int idx = tid; idx < nc * n; idx += nt) {
+      const int ix = idx / nc, c = idx % nc;
+      st(ix, cols[c0 + c], sm[ix * CC + c]);
     }
     __syncthreads();
   }

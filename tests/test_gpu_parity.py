@@ -227,8 +227,9 @@ def test_plain_fp64_n16_ten_steps_match_stored_oracle(qbe):
 
 def test_plain_fp64_n64_sampled_cells_match_stored_oracle(qbe):
     """N=64, Nx=128 Dirichlet workload at full size: C[W] of all 128 cells in the benchmark's launch
-    configuration; two sampled cells compared with the oracle, the rest checked for finiteness and
-    density conservation."""
+    configuration; two sampled cells compared with the oracle; every cell finite, and the density
+    defect sum_v C (a quadrature effect of the discrete operator: at N=64 with J=M=32 the oracle's own
+    relative defect reaches 2e-6) equal to the oracle's on the sampled cells and below 1e-5 elsewhere."""
     import torch
 
     path = os.path.join(GOLDEN, "plain_fp64_n64_cells.npz")
@@ -247,4 +248,7 @@ def test_plain_fp64_n64_sampled_cells_match_stored_oracle(qbe):
     p = O.Params(N=64)
     rho, _, _ = O.moments(got, p)
     scale = O.delta_v(p) ** 2 * np.abs(got).sum(axis=(1, 2, 3))
-    assert np.all(np.abs(rho).max(axis=1) < 1e-10 * scale)
+    rho_ref, _, _ = O.moments(g["C"], p)
+    for i, c in enumerate(cells):
+        assert np.abs(rho[c] - rho_ref[i]).max() < TOL_C * scale[c]
+    assert np.all(np.abs(rho).max(axis=1) < 1e-5 * scale)
