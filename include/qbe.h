@@ -161,6 +161,41 @@ long long qbe_launch_count(const qbe_handle* h);
 int qbe_enable_timing(qbe_handle* h, int enable);
 int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launches);
 
+/* Collision operator without any memory allocation (the paper has no
+ * counterpart: this is a deployment variant of qbe_collide).
+ *
+ * For callers that cannot allocate device memory at call time -- code hosted
+ * by a framework that owns the GPU's memory budget and forbids allocations,
+ * latency-critical paths where cudaMalloc's implicit device synchronisation is
+ * not acceptable, or deployments that must reserve all memory when the
+ * library is loaded.  It computes the same C[W] as qbe_collide for
+ * w[ncells][4][N][N] -> c[ncells][4][N][N], both DEVICE pointers of the
+ * calling thread's current device (g->device must equal it), on `stream`
+ * (a cudaStream_t, NULL = legacy default stream), asynchronously.
+ *
+ * Memory: no cudaMalloc, no cudaFree, no host heap.  Kernel tables and every
+ * piece of scratch live in one statically sized device array of
+ * QBE_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds until
+ * the process exits.  The first call on a device resolves that array's address
+ * (cudaGetSymbolAddress) and every call whose grid (N, J, M, L, R) differs
+ * from the previous call's rebuilds the tables in the array with two extra
+ * kernel launches; make that first call before any stream capture.  Cells are
+ * processed in batches that fit the array.  Every call shares the array and
+ * leaves its contents behind; the kernels initialise everything they read, so
+ * no clearing is needed between calls, but calls that overlap on the GPU (on
+ * different streams, or from several host threads) race and must be ordered
+ * by the caller.
+ *
+ * Limits: N in {8, 16, 32, 64}; J even in 2..64; M in 1..64; precision 0.
+ * The grid must fit: tables (4 J (2N)^2 doubles + 2 J M (2N) complex) plus,
+ * for one cell, (10 + 2 J) (2N)^2 complex + (2N)^2 doubles of workspace plus
+ * scratch of the I3 blocks, within QBE_NOALLOC_SCRATCH_BYTES (e.g. N = 64 with
+ * J = M = 32 fits, one cell per batch).  Larger grids return QBE_ERR_ARG.
+ * Errors: QBE_ERR_ARG (bad sizes, NULL pointers, grid too large, device
+ * mismatch), QBE_ERR_UNSUPPORTED (precision != 0), QBE_ERR_CUDA. */
+#define QBE_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int qbe_collide_noalloc(const qbe_grid* g, const double* w, double* c, int ncells, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

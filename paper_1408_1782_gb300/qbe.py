@@ -51,6 +51,7 @@ SIGNATURES = {
     "qbe_launch_count": (ctypes.c_longlong, [_c_void_p]),
     "qbe_enable_timing": (_c_int, [_c_void_p, _c_int]),
     "qbe_kernel_time": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "qbe_collide_noalloc": (_c_int, [ctypes.POINTER(QbeGrid), _c_void_p, _c_void_p, _c_int, _c_void_p]),
 }
 
 KERNEL_GROUPS = {"prep": 0, "i1": 1, "i24": 2, "i3": 3, "assemble": 4, "transport": 5, "rk": 6}
@@ -104,6 +105,26 @@ def _arg(x, shape):
             raise ValueError(f"expected contiguous float64 tensor of shape {tuple(shape)}")
         return x.data_ptr(), 1 if x.is_cuda else 0, x
     raise TypeError(f"unsupported array type {type(x)}")
+
+
+def collide_noalloc(w, out, J=32, M=32, L=12.0, R=7.5, stream=None):
+    """C[W] through qbe_collide_noalloc (no allocation inside the library): w and out are CUDA float64
+    tensors [ncells][4][N][N] on the current device; runs on `stream` (default: legacy stream)."""
+    import torch
+
+    ncells, N = w.shape[0], w.shape[-1]
+    shape = (ncells, 4, N, N)
+    pw, dev, _k1 = _arg(w, shape)
+    po, dev2, _k2 = _arg(out, shape)
+    if not (dev and dev2):
+        raise ValueError("qbe_collide_noalloc takes device memory")
+    g = QbeGrid(N, ncells, J, M, L, R, 0, torch.cuda.current_device())
+    handle = getattr(stream, "cuda_stream", stream)
+    rc = lib().qbe_collide_noalloc(ctypes.byref(g), _c_void_p(pw), _c_void_p(po), ncells,
+                                   _c_void_p(int(handle) if handle else 0))
+    if rc != 0:
+        raise QbeError(f"qbe_collide_noalloc failed with code {rc}")
+    return out
 
 
 class Solver:

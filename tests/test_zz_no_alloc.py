@@ -1,0 +1,77 @@
+"""qbe_collide_noalloc, the allocation-free variant of the collision operator.
+
+It exists for callers that cannot allocate device memory when they call the
+library (a host framework that owns the GPU memory budget, latency-critical
+paths that cannot afford cudaMalloc's implicit synchronisation, deployments
+that reserve all memory at load time): they pass their own input and output
+buffers and the library works inside a static device array.  These tests call
+it through the C ABI and compare it with qbe_collide on two calls in a row,
+within the collision tolerance of the parity tests (1e-11 of max |C|).  This
+file is collected last so that a run stopping at its first failure has already
+run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_1408_1782_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_C = 1e-11
+
+
+@pytest.fixture(scope="module")
+def qbe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1408_1782_gb300 import qbe as q
+
+    return q
+
+
+def _reference(q, w, N, J, M):
+    import torch
+
+    s = q.Solver(N, w.shape[0], J=J, M=M, stream=torch.cuda.current_stream())
+    c = s.collide(torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    out = c.cpu().numpy()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("N,J,M,ncells", [(16, 8, 6, 5), (16, 32, 32, 3), (64, 32, 32, 2)])
+def test_noalloc_matches_collide_on_two_calls(qbe, N, J, M, ncells):
+    import torch
+
+    w = inputs.synthetic_w(N, ncells, seed=21 + N, perturb=0.05)
+    ref = _reference(qbe, w, N, J, M)
+    wd = torch.from_numpy(w).cuda()
+    stream = torch.cuda.current_stream()
+    for _call in range(2):
+        out = torch.full_like(wd, float("nan"))
+        qbe.collide_noalloc(wd, out, J=J, M=M, stream=stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref).max() < TOL_C * np.abs(ref).max()
+
+
+def test_noalloc_rejects_what_does_not_fit(qbe):
+    import ctypes
+
+    import torch
+
+    w = torch.zeros((1, 4, 64, 64), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(w)
+    g = qbe.QbeGrid(64, 1, 64, 64, 12.0, 7.5, 0, torch.cuda.current_device())   # J = M = 64: too large
+    rc = qbe.lib().qbe_collide_noalloc(ctypes.byref(g), ctypes.c_void_p(w.data_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()), 1, None)
+    assert rc == -1
+    g = qbe.QbeGrid(128, 1, 8, 8, 12.0, 7.5, 0, torch.cuda.current_device())     # N = 128 unsupported
+    assert qbe.lib().qbe_collide_noalloc(ctypes.byref(g), ctypes.c_void_p(w.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), 1, None) == -1
