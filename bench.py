@@ -40,11 +40,16 @@ sys.path.insert(0, ROOT)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (profiles/fp64_fp32_issue_rates.md)
+FP32_FMA_PER_CLK_PER_SM = 128        # measured 116 FFMA/clk/SM
 
 
-def workload():
+def workload(name="plain_fp64_n64", precision=None):
     from paper_1408_1782_gb300 import inputs
-    return dict(inputs.WORKLOADS["plain_fp64_n64"])
+    wl = dict(inputs.WORKLOADS[name])
+    wl["name"] = name
+    if precision is not None:
+        wl["precision"] = precision
+    return wl
 
 
 def i3_flops_per_unit(N):
@@ -98,7 +103,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    wl = workload()
+    wl = workload(args.workload, args.precision)
     ncores = min(16, host_cores())
     times, cores = oracle_sample(wl, ncores, repeats=args.steps, warmup=args.warmup)
     T = sum(times)
@@ -110,7 +115,7 @@ def run_reference(args):
         "impl": "reference", "metric": "C[W] cell·k-pts/s", "value": value, "unit": "cell·k-pts/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Fermi-Dirac-perturbed W)",
+        "data": "synthetic (seeded Fermi-Dirac-perturbed W)", "impl_note": "FP64 CPU oracle",
         "config": config_dict(wl, args.gpus, reference=True),
         "cpu_baseline": {"value": value, "unit": "cell·k-pts/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "cell·k-pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -120,12 +125,16 @@ def run_reference(args):
 
 
 def config_dict(wl, ngpu, reference=False):
+    walls = {"dirichlet": "Dirichlet walls (Fermi-Dirac beta=1, mu=0)",
+             "maxwell": f"Maxwell walls (alpha={wl.get('alpha', 0)}, Fermi-Dirac beta=1, mu=0)",
+             "periodic": "periodic"}[wl["bc"]]
+    form = "plain FP64" if wl.get("precision", 0) == 0 else "FP32-split (FP32 collision transforms, FP64 rest)"
     return {
-        "workload": (f"plain FP64 at scale: {wl['N']}x{wl['N']} velocity grid, Nx={wl['Nx']} cells, "
-                     f"Dirichlet walls (Fermi-Dirac beta=1, mu=0), B=(0,0,0.5), dt={wl['dt']}, "
-                     f"J=M={wl['J']}, L={wl['L']}, R={wl['R']}, 5% perturbed synthetic W"),
+        "workload": (f"{wl['name']}: {form}, {wl['N']}x{wl['N']} velocity grid, Nx={wl['Nx']} cells, {walls}, "
+                     f"B={tuple(wl['B'])}, dt={wl['dt']}, J=M={wl['J']}, L={wl['L']}, R={wl['R']}, "
+                     f"{int(100 * wl['perturb'])}% perturbed synthetic W"),
         "N": wl["N"], "Nx": wl["Nx"], "J": wl["J"], "M": wl["M"], "dt": wl["dt"],
-        "bc": "dirichlet", "B": list(wl["B"]),
+        "bc": wl["bc"], "B": list(wl["B"]), "precision": "f64" if wl.get("precision", 0) == 0 else "f32-split",
         "l2": "256 MiB buffer zeroed before every timed step (working set also exceeds L2)",
         "parallelism": "oracle on host cores" if reference else ("single GPU" if ngpu == 1 else f"{ngpu} replicas"),
     }
@@ -208,14 +217,17 @@ def run_ours(args):
     g.build()
     from paper_1408_1782_gb300 import decomp, inputs, qbe
 
-    wl = workload()
+    wl = workload(args.workload, args.precision)
     if args.mode == "collide":
         return run_collide_only(args, wl, local)
     N, Nx = wl["N"], wl["Nx"]
+    prec = wl.get("precision", 0)
     stream = torch.cuda.current_stream()
-    s = qbe.Solver(N, Nx, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream)
-    fd = qbe.fd_state(wl["wall"]["beta"], wl["wall"]["mu_up"], wl["wall"]["mu_dn"])
-    s.set_boundary("dirichlet", fd, fd)
+    s = qbe.Solver(N, Nx, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream,
+                   precision=prec)
+    if wl["bc"] != "periodic":
+        fd = qbe.fd_state(wl["wall"]["beta"], wl["wall"]["mu_up"], wl["wall"]["mu_dn"])
+        s.set_boundary(wl["bc"], fd, fd, alpha=wl.get("alpha", 0.0))
     s.set_bfield(inputs.uniform_b(Nx, wl["B"]))
     W0 = inputs.synthetic_w(N, Nx, L=wl["L"], seed=0, perturb=wl["perturb"])
     s.set_state(W0)
@@ -282,8 +294,13 @@ def run_ours(args):
         sm_max = float(json.load(open(MEASURED_PEAKS)).get("sm_max_mhz", sm_max))
     except Exception:
         pass
-    peak = SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+    lanes = FP64_FMA_PER_CLK_PER_SM if prec == 0 else FP32_FMA_PER_CLK_PER_SM
+    peak = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
     total_group_ms = sum(v["ms"] for v in groups.values())
+
+    precision_report = None
+    if prec == 1 and rank == 0:
+        precision_report = fp32_split_report(wl, W0, local, qbe, torch, np)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -298,14 +315,16 @@ def run_ours(args):
             "metric": "C[W] cell·k-pts/s", "value": value, "unit": "cell·k-pts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "steps_per_s": 1e3 * args.steps / t_ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 0 else "f32-split",
             "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)",
             "config": config_dict(wl, world),
             "roofline": {"kernel": "k_i3 (Hu-Ying I3 term)", "bound": "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_i3_s * 1e3,
-                         "peak_source": (f"derived: {SM_COUNT} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x 2 "
-                                         f"flop x {sm_max:.0f} MHz (DFMA microbenchmark 1.20 TFLOP/s at 2002 MHz)")},
+                         "peak_source": (f"derived: {SM_COUNT} SMs x {lanes} {'FP64' if prec == 0 else 'FP32'} FMA/clk x 2 "
+                                         f"flop x {sm_max:.0f} MHz (microbenchmark: DFMA 1.20 TFLOP/s, FFMA 73.1 "
+                                         f"TFLOP/s at 2002 MHz)")},
             "kernel_share": {k: round(v["ms"] / total_group_ms, 4) for k, v in groups.items()},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "cell·k-pts/s", "h2d_bytes_per_step": state_bytes,
@@ -313,11 +332,57 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
         }
+        if precision_report is not None:
+            line["precision_report"] = precision_report
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def fp32_split_report(wl, W0, local, qbe, torch, np):
+    """FP32-split C[W] against the plain FP64 GPU form on a sample of cells (speed and error), and
+    against the stored FP64 oracle cells of this workload when present."""
+    N, J, M = wl["N"], wl["J"], wl["M"]
+    ncell = min(16, wl["Nx"])
+    w = torch.from_numpy(np.ascontiguousarray(W0[:ncell])).cuda()
+    out = {}
+    res = {}
+    for prec in (0, 1):
+        s = qbe.Solver(N, ncell, J=J, M=M, L=wl["L"], R=wl["R"], device=local,
+                       stream=torch.cuda.current_stream(), precision=prec)
+        c = s.collide(w)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.collide(w, c)
+        e1.record()
+        torch.cuda.synchronize()
+        res[prec] = (c.cpu().numpy(), e0.elapsed_time(e1))
+        s.close()
+    ref, t64 = res[0]
+    got, t32 = res[1]
+    out["sample_cells"] = ncell
+    out["ms_fp64_gpu"] = t64
+    out["ms_fp32_split"] = t32
+    out["speedup_vs_fp64_gpu"] = t64 / t32
+    out["max_rel_err_vs_fp64_gpu"] = float(np.abs(got - ref).max() / np.abs(ref).max())
+    out["tolerance_max_rel"] = 5e-6
+    gold = os.path.join(ROOT, "tests", "golden",
+                        "precision_n128_cells.npz" if N == 128 else "plain_fp64_n64_cells.npz")
+    if os.path.exists(gold):
+        g = np.load(gold)
+        s = qbe.Solver(N, len(g["cells"]), J=J, M=M, L=wl["L"], R=wl["R"], device=local,
+                       stream=torch.cuda.current_stream(), precision=1)
+        c = s.collide(torch.from_numpy(g["W"]).cuda()).cpu().numpy()
+        s.close()
+        out["max_rel_err_vs_oracle_cells"] = float(np.abs(c - g["C"]).max() / np.abs(g["C"]).max())
+        out["paper_norm_err_vs_oracle_cells"] = float(max(
+            sum(np.abs(c[i, k] - g["C"][i, k]).sum() / np.abs(g["C"][i, k]).sum() for k in range(4))
+            for i in range(c.shape[0])))
+        out["tolerance_paper_norm"] = 5e-5
+    return out
 
 
 def run_collide_only(args, wl, local):
@@ -329,7 +394,8 @@ def run_collide_only(args, wl, local):
     N = wl["N"]
     cells = args.cells or wl["Nx"]
     stream = torch.cuda.current_stream()
-    s = qbe.Solver(N, cells, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream)
+    s = qbe.Solver(N, cells, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream,
+                   precision=wl.get("precision", 0))
     W = inputs.synthetic_w(N, wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])[:cells]
     w = torch.from_numpy(W.copy()).cuda()
     c = torch.empty_like(w)
@@ -349,7 +415,8 @@ def run_collide_only(args, wl, local):
     line = {"mode": "collide", "metric": "C[W] cell·k-pts/s", "value": args.steps * cells * N * N / (t_ms * 1e-3),
             "unit": "cell·k-pts/s", "cells": cells, "steps": args.steps, "warmup": args.warmup,
             "ms_per_eval": t_ms / args.steps, "i3_ms_per_launch": i3_ms / max(i3_n, 1),
-            "i3_tflops": flops / (i3_ms / max(i3_n, 1) * 1e-3) / 1e12, "dtype": "f64"}
+            "i3_tflops": flops / (i3_ms / max(i3_n, 1) * 1e-3) / 1e12,
+            "dtype": "f64" if wl.get("precision", 0) == 0 else "f32-split", "workload": wl["name"]}
     print(json.dumps(line), flush=True)
     s.close()
     return 0
@@ -364,6 +431,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["step", "collide"], default="step")
+    ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128"], default="plain_fp64_n64")
+    ap.add_argument("--precision", type=int, choices=[0, 1], default=None)
     ap.add_argument("--cells", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":

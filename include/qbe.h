@@ -16,7 +16,8 @@
  *    v = (2L/N) * (ix - N/2, iy - N/2), i.e. v in (2L/N) Xi with
  *    Xi = {-N/2..N/2-1}^2 (Sec. 3.2 eq. fourier_grid, Sec. 5.1).
  *  - Cell centres x_j = (j + 1/2)/Nx.
- *  - Arithmetic is IEEE FP64 throughout.
+ *  - Arithmetic is IEEE FP64 throughout, except the collision transforms of
+ *    the FP32-split form (qbe_grid.precision = 1).
  *  - Pointers: "on_device" = 1 means the pointer is device memory of the
  *    handle's GPU; 0 means host memory.  The caller owns every pointer it
  *    passes; the library copies host inputs before returning and never keeps
@@ -48,8 +49,11 @@ extern "C" {
  * the half circle (eq. theta_grid; even, 2..64); M Gauss-Legendre radial nodes
  * (eq. approxH-JM; 1..64); L half-width of the periodised velocity box
  * [-L, L]^2; R truncation radius of the collision integrals (B_R).
- * precision must be 0 (FP64).  The paper's values are L = 12, R = 7.5,
- * J = M = 32. */
+ * precision: 0 = plain FP64; 1 = FP32-split form (the collision operator's
+ * transforms, products and per-unit accumulations in FP32; its input, output
+ * and the reduction of its per-unit partial sums, the transport with its
+ * boundary projections, the RK2 accumulation and the moments in FP64).  The
+ * paper's values are L = 12, R = 7.5, J = M = 32. */
 typedef struct qbe_grid {
   int N;
   int Nx;

@@ -6,31 +6,53 @@ namespace qbe {
 
 cudaError_t collide_batch(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells,
                           cudaStream_t s, long long& launches, KernelTimer* tm) {
+  if (cw.prec == 1) {
+    switch (t.n) {
+      case 16: return collide_batch_n<16, float>(t, cw, w, c, ncells, s, launches, tm);
+      case 32: return collide_batch_n<32, float>(t, cw, w, c, ncells, s, launches, tm);
+      case 64: return collide_batch_n<64, float>(t, cw, w, c, ncells, s, launches, tm);
+      case 128: return collide_batch_n<128, float>(t, cw, w, c, ncells, s, launches, tm);
+      case 256: return collide_batch_n<256, float>(t, cw, w, c, ncells, s, launches, tm);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (t.n) {
-    case 16: return collide_batch_n<16>(t, cw, w, c, ncells, s, launches, tm);
-    case 32: return collide_batch_n<32>(t, cw, w, c, ncells, s, launches, tm);
-    case 64: return collide_batch_n<64>(t, cw, w, c, ncells, s, launches, tm);
-    case 128: return collide_batch_n<128>(t, cw, w, c, ncells, s, launches, tm);
-    case 256: return collide_batch_n<256>(t, cw, w, c, ncells, s, launches, tm);
+    case 16: return collide_batch_n<16, double>(t, cw, w, c, ncells, s, launches, tm);
+    case 32: return collide_batch_n<32, double>(t, cw, w, c, ncells, s, launches, tm);
+    case 64: return collide_batch_n<64, double>(t, cw, w, c, ncells, s, launches, tm);
+    case 128: return collide_batch_n<128, double>(t, cw, w, c, ncells, s, launches, tm);
+    case 256: return collide_batch_n<256, double>(t, cw, w, c, ncells, s, launches, tm);
     default: return cudaErrorInvalidValue;
   }
 }
 
 
-cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw) {
+cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int prec) {
   const size_t P = (size_t)t.n * t.n;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int bps = 1;
-  switch (t.n) {
-    case 16: bps = i3_blocks_per_sm<16>(); break;
-    case 32: bps = i3_blocks_per_sm<32>(); break;
-    case 64: bps = i3_blocks_per_sm<64>(); break;
-    case 128: bps = i3_blocks_per_sm<128>(); break;
-    case 256: bps = i3_blocks_per_sm<256>(); break;
-    default: return cudaErrorInvalidValue;
+  if (prec == 1) {
+    switch (t.n) {
+      case 16: bps = i3_blocks_per_sm<16, float>(); break;
+      case 32: bps = i3_blocks_per_sm<32, float>(); break;
+      case 64: bps = i3_blocks_per_sm<64, float>(); break;
+      case 128: bps = i3_blocks_per_sm<128, float>(); break;
+      case 256: bps = i3_blocks_per_sm<256, float>(); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (t.n) {
+      case 16: bps = i3_blocks_per_sm<16, double>(); break;
+      case 32: bps = i3_blocks_per_sm<32, double>(); break;
+      case 64: bps = i3_blocks_per_sm<64, double>(); break;
+      case 128: bps = i3_blocks_per_sm<128, double>(); break;
+      case 256: bps = i3_blocks_per_sm<256, double>(); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
+  cw.prec = prec;
   cw.nb = nb;
   cw.grid_i3 = nsm * bps;
   // enough (cell, j, m-chunk) units for about 8 waves of the persistent grid
@@ -45,16 +67,18 @@ cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw) {
   if (3 * (size_t)cw.grid_i3 > ws_fields) ws_fields = 3 * (size_t)cw.grid_i3;
   cw.ws_fields = ws_fields;
   const size_t N = t.N;
+  const size_t cz = prec == 1 ? sizeof(float2) : sizeof(double2);   // complex element
+  const size_t rz = cz / 2;                                           // real element
   cudaError_t e;
 #define QBE_ALLOC(ptr, bytes) \
   if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) { free_collision_work(cw); return e; }
-  QBE_ALLOC(cw.what, (size_t)nb * 4 * P * sizeof(double2));
-  QBE_ALLOC(cw.wfine, (size_t)nb * 2 * P * sizeof(double2));
-  QBE_ALLOC(cw.Dacc, (size_t)nb * 2 * P * sizeof(double2));
-  QBE_ALLOC(cw.K2acc, (size_t)nb * P * sizeof(double));
-  QBE_ALLOC(cw.K4acc, (size_t)nb * 2 * P * sizeof(double2));
-  QBE_ALLOC(cw.K3part, nparts * 2 * P * sizeof(double2));
-  QBE_ALLOC(cw.ws, ws_fields * P * sizeof(double2));
+  QBE_ALLOC(cw.what, (size_t)nb * 4 * P * cz);
+  QBE_ALLOC(cw.wfine, (size_t)nb * 2 * P * cz);
+  QBE_ALLOC(cw.Dacc, (size_t)nb * 2 * P * cz);
+  QBE_ALLOC(cw.K2acc, (size_t)nb * P * rz);
+  QBE_ALLOC(cw.K4acc, (size_t)nb * 2 * P * cz);
+  QBE_ALLOC(cw.K3part, nparts * 2 * P * cz);
+  QBE_ALLOC(cw.ws, ws_fields * P * cz);
   QBE_ALLOC(cw.cbuf, (size_t)nb * 4 * N * N * sizeof(double));
   QBE_ALLOC(cw.wbuf, (size_t)nb * 4 * N * N * sizeof(double));
 #undef QBE_ALLOC

@@ -25,6 +25,11 @@
 //     so the I2 and I4 inverse transforms are shared;
 //   * I3: the weight (pi/J) w_m is split as sqrt((pi/J) w_m) into both shifted
 //     factors; each accumulated K3 term carries it exactly once.
+//
+// Precision: every kernel is a template on the real type T of its transforms,
+// products and per-unit accumulations (double: the plain FP64 form; float: the
+// FP32-split form).  The state W comes in and C[W] goes out in FP64, and the
+// reduction of the per-unit K3 partial sums is done in FP64 in both forms.
 #pragma once
 
 #include <cmath>
@@ -46,10 +51,15 @@ __device__ __forceinline__ bool in_xi(int k) {
   return (k < N / 2) || (k > n - N / 2);
 }
 
-template <int n>
-__device__ __forceinline__ void zero_fields(double2* p, int count) {
-  for (int i = threadIdx.x; i < count; i += blockDim.x) p[i] = make_double2(0.0, 0.0);
+template <class C2>
+__device__ __forceinline__ void zero_fields(C2* p, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) p[i] = mk2((typename RealOf<C2>::type)0, (typename RealOf<C2>::type)0);
   __syncthreads();
+}
+
+template <class T>
+__device__ __forceinline__ typename Vec2Of<T>::type zero2() {
+  return mk2((T)0, (T)0);
 }
 
 // --------------------------------------------------------------------------
@@ -60,46 +70,48 @@ __device__ __forceinline__ void zero_fields(double2* p, int count) {
 // The coarse DFT is the fine forward FFT of the zero-interleaved samples
 // (its spectrum repeats with period N), scaled by 1/N^2 and cut to Xi.
 // --------------------------------------------------------------------------
-template <int n>
-__global__ void __launch_bounds__(kThreads) k_prep(const double* __restrict__ w, double2* what, double2* wfine,
-                                                   double2* ws, const double2* __restrict__ gtw) {
-  extern __shared__ double2 smem[];
-  double2* tw = smem;
-  double2* sm = smem + n;
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads) k_prep(const double* __restrict__ w, typename Vec2Of<T>::type* what,
+                                                   typename Vec2Of<T>::type* wfine, typename Vec2Of<T>::type* ws,
+                                                   const typename Vec2Of<T>::type* __restrict__ gtw) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
   load_twiddles<n>(tw, gtw);
   constexpr int N = n / 2, P = n * n;
   const int c = blockIdx.x;
   const double* wc = w + (size_t)c * 4 * N * N;
-  double2* G = ws + (size_t)blockIdx.x * P;
-  const double invN2 = 1.0 / ((double)N * N);
+  C2* G = ws + (size_t)blockIdx.x * P;
+  const T invN2 = (T)(1.0 / ((double)N * N));
   for (int q = 0; q < 4; ++q) {
     const int a = (q == 0) ? 0 : (q == 1) ? 2 : (q == 2) ? 1 : 3;
     const int b = (q == 0) ? 1 : (q == 1) ? 3 : (q == 2) ? 2 : -1;
     row_pass<n, -1, false, 0>(
         sm, tw,
         [&](int ix, int iy) {
-          if ((ix | iy) & 1) return make_double2(0.0, 0.0);
+          if ((ix | iy) & 1) return zero2<T>();
           const int i = ix >> 1, j = iy >> 1;
-          return make_double2(wc[(a * N + i) * N + j], b >= 0 ? wc[(b * N + i) * N + j] : 0.0);
+          return mk2((T)wc[(a * N + i) * N + j], b >= 0 ? (T)wc[(b * N + i) * N + j] : (T)0);
         },
-        NoMid(), [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
-    double2* out = what + ((size_t)c * 4 + q) * P;
+        NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+    C2* out = what + ((size_t)c * 4 + q) * P;
     col_pass<n, -1, false, 0>(
         sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, double2 v) {
+        [&](int ix, int iy, C2 v) {
           const bool keep = in_xi<n>(freq_of_pos<n>(ix)) && in_xi<n>(freq_of_pos<n>(iy));
-          out[ix * n + iy] = keep ? cscale(v, invN2) : make_double2(0.0, 0.0);
+          out[ix * n + iy] = keep ? cscale(v, invN2) : zero2<T>();
         });
   }
   for (int p = 0; p < 2; ++p) {
-    const double2* in = what + ((size_t)c * 4 + p) * P;
-    double2* out = wfine + ((size_t)c * 2 + p) * P;
+    const C2* in = what + ((size_t)c * 4 + p) * P;
+    C2* out = wfine + ((size_t)c * 2 + p) * P;
     col_pass<n, 1, false, 0>(
         sm, tw, [&](int ix, int iy) { return in[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
+        [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
     row_pass<n, 1, false, 0>(
         sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, double2 v) { out[ix * n + iy] = v; });
+        [&](int ix, int iy, C2 v) { out[ix * n + iy] = v; });
   }
 }
 
@@ -107,40 +119,42 @@ __global__ void __launch_bounds__(kThreads) k_prep(const double* __restrict__ w,
 // I1 (conservative part): D^_b(sigma) = sum_j' K_j'(sigma) FFT[(2w0-1) IFFT(phi'_j' w_b^)].
 // One block per cell; pairs (w1 + i w2) and (w3).
 // --------------------------------------------------------------------------
-template <int n>
-__global__ void __launch_bounds__(kThreads) k_i1(const double2* what, const double2* wfine, double2* Dacc,
-                                                 double2* ws, const double2* __restrict__ gtw,
-                                                 const double* __restrict__ phip, const double* __restrict__ Ktab,
-                                                 int J) {
-  extern __shared__ double2 smem[];
-  double2* tw = smem;
-  double2* sm = smem + n;
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads) k_i1(const typename Vec2Of<T>::type* what,
+                                                 const typename Vec2Of<T>::type* wfine, typename Vec2Of<T>::type* Dacc,
+                                                 typename Vec2Of<T>::type* ws,
+                                                 const typename Vec2Of<T>::type* __restrict__ gtw,
+                                                 const T* __restrict__ phip, const T* __restrict__ Ktab, int J) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
   const int c = blockIdx.x;
-  double2* G = ws + (size_t)blockIdx.x * P;
-  double2* D = Dacc + (size_t)c * 2 * P;
-  zero_fields<n>(D, 2 * P);
-  const double2* wf0 = wfine + (size_t)c * 2 * P;
+  C2* G = ws + (size_t)blockIdx.x * P;
+  C2* D = Dacc + (size_t)c * 2 * P;
+  zero_fields(D, 2 * P);
+  const C2* wf0 = wfine + (size_t)c * 2 * P;
   for (int jp = 0; jp < J; ++jp) {
-    const double* ph = phip + (size_t)jp * P;
-    const double* K = Ktab + (size_t)jp * P;
+    const T* ph = phip + (size_t)jp * P;
+    const T* K = Ktab + (size_t)jp * P;
     for (int p = 0; p < 2; ++p) {
-      const double2* in = what + ((size_t)c * 4 + 2 + p) * P;
-      double2* Dp = D + (size_t)p * P;
+      const C2* in = what + ((size_t)c * 4 + 2 + p) * P;
+      C2* Dp = D + (size_t)p * P;
       col_pass<n, 1, false, 0>(
           sm, tw, [&](int ix, int iy) { return cscale(in[ix * n + iy], ph[ix * n + iy]); }, NoMid(),
-          [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
+          [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
       row_pass<n, 1, true, -1>(
           sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
-          [&](int ix, int iy, double2 v) { return cscale(v, 2.0 * wf0[ix * n + iy].x - 1.0); },
-          [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
+          [&](int ix, int iy, C2 v) { return cscale(v, (T)2 * wf0[ix * n + iy].x - (T)1); },
+          [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
       col_pass<n, -1, false, 0>(
           sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
-          [&](int ix, int iy, double2 v) {
-            const double k = K[ix * n + iy];
-            const double2 d = Dp[ix * n + iy];
-            Dp[ix * n + iy] = make_double2(fma(k, v.x, d.x), fma(k, v.y, d.y));
+          [&](int ix, int iy, C2 v) {
+            const T k = K[ix * n + iy];
+            const C2 d = Dp[ix * n + iy];
+            Dp[ix * n + iy] = mk2(fmaT(k, v.x, d.x), fmaT(k, v.y, d.y));
           });
     }
   }
@@ -152,62 +166,65 @@ __global__ void __launch_bounds__(kThreads) k_i1(const double2* what, const doub
 //   K2  += 2 (pi/J) sum_a eta_a F_{a,j} F_{a,j+J/2}
 //   K4^ += (pi/J) [psi_j FFT((2w0-1) F_{.,j+J/2}) + psi_{j+J/2} FFT((2w0-1) F_{.,j})] / n^2
 // --------------------------------------------------------------------------
-template <int n>
-__global__ void __launch_bounds__(kThreads) k_i24(const double2* what, const double2* wfine, double* K2acc,
-                                                  double2* K4acc, double2* ws, const double2* __restrict__ gtw,
-                                                  const double* __restrict__ psi, int J) {
-  extern __shared__ double2 smem[];
-  double2* tw = smem;
-  double2* sm = smem + n;
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads) k_i24(const typename Vec2Of<T>::type* what,
+                                                  const typename Vec2Of<T>::type* wfine, T* K2acc,
+                                                  typename Vec2Of<T>::type* K4acc, typename Vec2Of<T>::type* ws,
+                                                  const typename Vec2Of<T>::type* __restrict__ gtw,
+                                                  const T* __restrict__ psi, int J) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
   const int c = blockIdx.x;
-  double2* slot = ws + (size_t)blockIdx.x * 5 * P;
-  double2* FA = slot;            // [2][P]
-  double2* FB = slot + 2 * P;    // [2][P]
-  double2* G = slot + 4 * P;
-  double* K2 = K2acc + (size_t)c * P;
-  double2* K4 = K4acc + (size_t)c * 2 * P;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) K2[i] = 0.0;
-  zero_fields<n>(K4, 2 * P);
-  const double2* wf0 = wfine + (size_t)c * 2 * P;
-  const double wj = kPi / J;
-  const double scale = wj / (double)P;
+  C2* slot = ws + (size_t)blockIdx.x * 5 * P;
+  C2* FA = slot;            // [2][P]
+  C2* FB = slot + 2 * P;    // [2][P]
+  C2* G = slot + 4 * P;
+  T* K2 = K2acc + (size_t)c * P;
+  C2* K4 = K4acc + (size_t)c * 2 * P;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) K2[i] = (T)0;
+  zero_fields(K4, 2 * P);
+  const C2* wf0 = wfine + (size_t)c * 2 * P;
+  const T wj = (T)(kPi / J);
+  const T scale = (T)(kPi / J / (double)P);
   for (int j = 0; j < J / 2; ++j) {
     const int jp = j + J / 2;
     for (int p = 0; p < 2; ++p) {
-      const double2* in = what + ((size_t)c * 4 + p) * P;
+      const C2* in = what + ((size_t)c * 4 + p) * P;
       for (int h = 0; h < 2; ++h) {
-        const double* ps = psi + (size_t)(h == 0 ? j : jp) * P;
-        double2* F = (h == 0 ? FA : FB) + (size_t)p * P;
+        const T* ps = psi + (size_t)(h == 0 ? j : jp) * P;
+        C2* F = (h == 0 ? FA : FB) + (size_t)p * P;
         col_pass<n, 1, false, 0>(
             sm, tw, [&](int ix, int iy) { return cscale(in[ix * n + iy], ps[ix * n + iy]); }, NoMid(),
-            [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
+            [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
         row_pass<n, 1, false, 0>(
             sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
-            [&](int ix, int iy, double2 v) { F[ix * n + iy] = v; });
+            [&](int ix, int iy, C2 v) { F[ix * n + iy] = v; });
       }
     }
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-      const double2 a0 = FA[i], a1 = FA[P + i], b0 = FB[i], b1 = FB[P + i];
-      const double s = a0.x * b0.x - a0.y * b0.y - a1.x * b1.x - a1.y * b1.y;
-      K2[i] = fma(2.0 * wj, s, K2[i]);
+      const C2 a0 = FA[i], a1 = FA[P + i], b0 = FB[i], b1 = FB[P + i];
+      const T s = a0.x * b0.x - a0.y * b0.y - a1.x * b1.x - a1.y * b1.y;
+      K2[i] = fmaT((T)2 * wj, s, K2[i]);
     }
     __syncthreads();
     for (int p = 0; p < 2; ++p) {
-      double2* K4p = K4 + (size_t)p * P;
+      C2* K4p = K4 + (size_t)p * P;
       for (int h = 0; h < 2; ++h) {
-        const double2* F = (h == 0 ? FB : FA) + (size_t)p * P;   // psi_j pairs with F_{j+J/2}
-        const double* ps = psi + (size_t)(h == 0 ? j : jp) * P;
+        const C2* F = (h == 0 ? FB : FA) + (size_t)p * P;   // psi_j pairs with F_{j+J/2}
+        const T* ps = psi + (size_t)(h == 0 ? j : jp) * P;
         row_pass<n, -1, false, 0>(
-            sm, tw, [&](int ix, int iy) { return cscale(F[ix * n + iy], 2.0 * wf0[ix * n + iy].x - 1.0); },
-            NoMid(), [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
+            sm, tw, [&](int ix, int iy) { return cscale(F[ix * n + iy], (T)2 * wf0[ix * n + iy].x - (T)1); },
+            NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
         col_pass<n, -1, false, 0>(
             sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
-            [&](int ix, int iy, double2 v) {
-              const double k = scale * ps[ix * n + iy];
-              const double2 d = K4p[ix * n + iy];
-              K4p[ix * n + iy] = make_double2(fma(k, v.x, d.x), fma(k, v.y, d.y));
+            [&](int ix, int iy, C2 v) {
+              const T k = scale * ps[ix * n + iy];
+              const C2 d = K4p[ix * n + iy];
+              K4p[ix * n + iy] = mk2(fmaT(k, v.x, d.x), fmaT(k, v.y, d.y));
             });
       }
     }
@@ -222,83 +239,84 @@ __global__ void __launch_bounds__(kThreads) k_i24(const double2* what, const dou
 // The unit's partial sum acc[2][n*n] (pairs (0,1), (2,3), real space) is
 // written to its own slot of K3part and reduced in fixed order later.
 // --------------------------------------------------------------------------
-template <int n>
-__global__ void __launch_bounds__(kThreads, 3) k_i3(const double2* what, const double2* wfine, double2* K3part,
-                                                 double2* ws, const double2* __restrict__ gtw,
-                                                 const double* __restrict__ psip_s,
-                                                 const double2* __restrict__ phase, int J, int M, int nmc, int mch,
-                                                 int nunits) {
-  extern __shared__ double2 smem[];
-  double2* tw = smem;
-  double2* sm = smem + n;
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads, 3) k_i3(const typename Vec2Of<T>::type* what,
+                                                    const typename Vec2Of<T>::type* wfine,
+                                                    typename Vec2Of<T>::type* K3part, typename Vec2Of<T>::type* ws,
+                                                    const typename Vec2Of<T>::type* __restrict__ gtw,
+                                                    const T* __restrict__ psip_s,
+                                                    const typename Vec2Of<T>::type* __restrict__ phase, int J, int M,
+                                                    int nmc, int mch, int nunits) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
   __shared__ int xcols[n];          // permuted positions whose frequency lies in Xi (incl. its -N/2 line)
   __shared__ unsigned char xmask[n];
   if (threadIdx.x == 0) {
-    int c = 0;
+    int cnt = 0;
     for (int pos = 0; pos < n; ++pos) {
       const int k = freq_of_pos<n>(pos);
       const bool in = (k < n / 4) || (k >= n - n / 4);
       xmask[pos] = in ? 1 : 0;
-      if (in) xcols[c++] = pos;
+      if (in) xcols[cnt++] = pos;
     }
   }
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
-  double2* slot = ws + (size_t)blockIdx.x * 3 * P;
-  double2* Sig = slot;           // [2][P]
-  double2* G = slot + 2 * P;
+  C2* slot = ws + (size_t)blockIdx.x * 3 * P;
+  C2* Sig = slot;           // [2][P]
+  C2* G = slot + 2 * P;
   for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
     const int c = unit / (J * nmc);
     const int j = (unit / nmc) % J;
     const int mc = unit % nmc;
-    double2* acc = K3part + (size_t)unit * 2 * P;
-    zero_fields<n>(acc, 2 * P);
-    const double* psp = psip_s + (size_t)j * P;
-    const double2* wf = wfine + (size_t)c * 2 * P;
+    C2* acc = K3part + (size_t)unit * 2 * P;
+    zero_fields(acc, 2 * P);
+    const T* psp = psip_s + (size_t)j * P;
+    const C2* wf = wfine + (size_t)c * 2 * P;
     const int m0 = mc * mch, m1 = min(M, m0 + mch);
     for (int m = m0; m < m1; ++m) {
-      const double2* px = phase + ((size_t)j * M + m) * 2 * n;
-      const double2* py = px + n;
+      const C2* px = phase + ((size_t)j * M + m) * 2 * n;
+      const C2* py = px + n;
       for (int p = 0; p < 2; ++p) {
-        const double2* in = what + ((size_t)c * 4 + p) * P;
-        double2* S = Sig + (size_t)p * P;
+        const C2* in = what + ((size_t)c * 4 + p) * P;
+        C2* S = Sig + (size_t)p * P;
         // only the n/2 columns (y frequencies) of Xi are non-zero: transform those
         col_pass_list<n, 1, false, 0>(
             sm, tw, xcols, n / 2,
-            [&](int ix, int iy) {
-              return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : make_double2(0.0, 0.0);
-            },
-            NoMid(), [&](int ix, int iy, double2 v) { S[ix * n + iy] = v; });
+            [&](int ix, int iy) { return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<T>(); },
+            NoMid(), [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
         row_pass<n, 1, false, 0>(
-            sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : make_double2(0.0, 0.0); }, NoMid(),
-            [&](int ix, int iy, double2 v) { S[ix * n + iy] = v; });
+            sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : zero2<T>(); }, NoMid(),
+            [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
       }
       for (int a = 0; a < 4; ++a) {
-        const double2* wa = wf + (size_t)(a >> 1) * P;
-        const double2* Sa = Sig + (size_t)(a >> 1) * P;
+        const C2* wa = wf + (size_t)(a >> 1) * P;
+        const C2* Sa = Sig + (size_t)(a >> 1) * P;
         const bool im = (a & 1) != 0;
-        const double eta = (a == 0) ? 1.0 : -1.0;
+        const T eta = (a == 0) ? (T)1 : (T)-1;
         for (int p = 0; p < 2; ++p) {
-          const double2* Sp = Sig + (size_t)p * P;
-          double2* accp = acc + (size_t)p * P;
+          const C2* Sp = Sig + (size_t)p * P;
+          C2* accp = acc + (size_t)p * P;
           row_pass<n, -1, false, 0>(
               sm, tw,
               [&](int ix, int iy) {
-                const double2 z = wa[ix * n + iy];
+                const C2 z = wa[ix * n + iy];
                 return cscale(Sp[ix * n + iy], im ? z.y : z.x);
               },
-              NoMid(), [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
+              NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
           col_conv_pass<n>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
               [&](int ix, int iy) { return psp[ix * n + iy]; },
-              [&](int ix, int iy, double2 v) { G[ix * n + iy] = v; });
+              [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
           row_pass<n, 1, false, 0>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
-              [&](int ix, int iy, double2 v) {
-                const double2 s = Sa[ix * n + iy];
-                const double f = eta * (im ? s.y : s.x);
-                const double2 d = accp[ix * n + iy];
-                accp[ix * n + iy] = make_double2(fma(f, v.x, d.x), fma(f, v.y, d.y));
+              [&](int ix, int iy, C2 v) {
+                const C2 s = Sa[ix * n + iy];
+                const T f = eta * (im ? s.y : s.x);
+                const C2 d = accp[ix * n + iy];
+                accp[ix * n + iy] = mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y));
               });
         }
       }
@@ -309,80 +327,84 @@ __global__ void __launch_bounds__(kThreads, 3) k_i3(const double2* what, const d
 // --------------------------------------------------------------------------
 // Assemble C on the fine grid from D, K2, K3, K4 (Pauli formulas of Sec. 3.1),
 // then FFT, cut to Xi (without the -N/2 line), inverse FFT and sample the
-// coarse nodes.  One block per cell.
+// coarse nodes.  One block per cell.  The K3 partial sums are added in FP64.
 // --------------------------------------------------------------------------
-template <int n>
-__global__ void __launch_bounds__(kThreads) k_assemble(const double2* wfine, const double2* Dacc,
-                                                       const double* K2acc, const double2* K4acc,
-                                                       const double2* K3part, int nparts, double2* ws,
-                                                       const double2* __restrict__ gtw, double* cout) {
-  extern __shared__ double2 smem[];
-  double2* tw = smem;
-  double2* sm = smem + n;
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads) k_assemble(const typename Vec2Of<T>::type* wfine,
+                                                       const typename Vec2Of<T>::type* Dacc, const T* K2acc,
+                                                       const typename Vec2Of<T>::type* K4acc,
+                                                       const typename Vec2Of<T>::type* K3part, int nparts,
+                                                       typename Vec2Of<T>::type* ws,
+                                                       const typename Vec2Of<T>::type* __restrict__ gtw,
+                                                       double* cout) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
   load_twiddles<n>(tw, gtw);
   constexpr int N = n / 2, P = n * n;
   const int c = blockIdx.x;
-  double2* slot = ws + (size_t)blockIdx.x * 6 * P;
-  double2* B0 = slot;
+  C2* slot = ws + (size_t)blockIdx.x * 6 * P;
+  C2* B0 = slot;
   // D pairs -> slot[0], slot[1]; K4 pairs -> slot[2], slot[3] (inverse 2-D transforms)
   for (int f = 0; f < 4; ++f) {
-    const double2* in = (f < 2) ? (Dacc + ((size_t)c * 2 + f) * P) : (K4acc + ((size_t)c * 2 + (f - 2)) * P);
-    double2* out = slot + (size_t)f * P;
+    const C2* in = (f < 2) ? (Dacc + ((size_t)c * 2 + f) * P) : (K4acc + ((size_t)c * 2 + (f - 2)) * P);
+    C2* out = slot + (size_t)f * P;
     col_pass<n, 1, false, 0>(
         sm, tw, [&](int ix, int iy) { return in[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, double2 v) { out[ix * n + iy] = v; });
+        [&](int ix, int iy, C2 v) { out[ix * n + iy] = v; });
     row_pass<n, 1, false, 0>(
         sm, tw, [&](int ix, int iy) { return out[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, double2 v) { out[ix * n + iy] = v; });
+        [&](int ix, int iy, C2 v) { out[ix * n + iy] = v; });
   }
-  const double2* parts = K3part + (size_t)c * nparts * 2 * P;
-  const double2* wf0 = wfine + (size_t)c * 2 * P;
-  const double2* wf1 = wf0 + P;
-  const double* K2 = K2acc + (size_t)c * P;
+  const C2* parts = K3part + (size_t)c * nparts * 2 * P;
+  const C2* wf0 = wfine + (size_t)c * 2 * P;
+  const C2* wf1 = wf0 + P;
+  const T* K2 = K2acc + (size_t)c * P;
   const double tp = 2.0 * kPi;
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    double2 k3a = make_double2(0.0, 0.0), k3b = make_double2(0.0, 0.0);
+    double k3ax = 0, k3ay = 0, k3bx = 0, k3by = 0;
     for (int u = 0; u < nparts; ++u) {
-      const double2 x = parts[(size_t)u * 2 * P + i];
-      const double2 y = parts[(size_t)u * 2 * P + P + i];
-      k3a.x += x.x; k3a.y += x.y; k3b.x += y.x; k3b.y += y.y;
+      const C2 x = parts[(size_t)u * 2 * P + i];
+      const C2 y = parts[(size_t)u * 2 * P + P + i];
+      k3ax += (double)x.x; k3ay += (double)x.y; k3bx += (double)y.x; k3by += (double)y.y;
     }
     const double w0 = wf0[i].x, w1 = wf0[i].y, w2 = wf1[i].x, w3 = wf1[i].y;
     const double D1 = slot[i].x, D2 = slot[i].y, D3 = slot[P + i].x;
-    const double K40 = slot[2 * P + i].x, K41 = -slot[2 * P + i].y;   // eta_b applied
-    const double K42 = -slot[3 * P + i].x, K43 = -slot[3 * P + i].y;
-    const double K30 = k3a.x, K31 = -k3a.y, K32 = -k3b.x, K33 = -k3b.y;
+    const double K40 = slot[2 * P + i].x, K41 = -(double)slot[2 * P + i].y;   // eta_b applied
+    const double K42 = -(double)slot[3 * P + i].x, K43 = -(double)slot[3 * P + i].y;
+    const double K30 = k3ax, K31 = -k3ay, K32 = -k3bx, K33 = -k3by;
     const double k2 = K2[i];
     const double C0 = tp * (k2 * (1.0 - w0) - K30 + w0 * K40 + w1 * K41 + w2 * K42 + w3 * K43);
     const double C1 = -2.0 * (D2 * w3 - D3 * w2) + tp * (-k2 * w1 - K31 + w0 * K41 + K40 * w1);
-    const double C2 = -2.0 * (D3 * w1 - D1 * w3) + tp * (-k2 * w2 - K32 + w0 * K42 + K40 * w2);
+    const double C2v = -2.0 * (D3 * w1 - D1 * w3) + tp * (-k2 * w2 - K32 + w0 * K42 + K40 * w2);
     const double C3 = -2.0 * (D1 * w2 - D2 * w1) + tp * (-k2 * w3 - K33 + w0 * K43 + K40 * w3);
-    B0[i] = make_double2(C0, C1);
-    B0[P + i] = make_double2(C2, C3);
+    B0[i] = mk2((T)C0, (T)C1);
+    B0[P + i] = mk2((T)C2v, (T)C3);
   }
   __syncthreads();
-  const double invP = 1.0 / (double)P;
+  const T invP = (T)(1.0 / (double)P);
   double* co = cout + (size_t)c * 4 * N * N;
-  double2* H = slot + 2 * P;
+  C2* H = slot + 2 * P;
   for (int p = 0; p < 2; ++p) {
-    const double2* F = B0 + (size_t)p * P;
+    const C2* F = B0 + (size_t)p * P;
     row_pass<n, -1, false, 0>(
         sm, tw, [&](int ix, int iy) { return F[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, double2 v) { H[ix * n + iy] = v; });
+        [&](int ix, int iy, C2 v) { H[ix * n + iy] = v; });
     col_pass<n, -1, true, 1>(
         sm, tw, [&](int ix, int iy) { return H[ix * n + iy]; },
-        [&](int ix, int iy, double2 v) {
+        [&](int ix, int iy, C2 v) {
           const bool keep = in_xi<n>(freq_of_pos<n>(ix)) && in_xi<n>(freq_of_pos<n>(iy));
-          return keep ? cscale(v, invP) : make_double2(0.0, 0.0);
+          return keep ? cscale(v, invP) : zero2<T>();
         },
-        [&](int ix, int iy, double2 v) { H[ix * n + iy] = v; });
+        [&](int ix, int iy, C2 v) { H[ix * n + iy] = v; });
     row_pass<n, 1, false, 0>(
         sm, tw, [&](int ix, int iy) { return H[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, double2 v) {
+        [&](int ix, int iy, C2 v) {
           if (((ix | iy) & 1) == 0) {
             const int i = ix >> 1, j = iy >> 1;
-            co[((2 * p) * N + i) * N + j] = v.x;
-            co[((2 * p + 1) * N + i) * N + j] = v.y;
+            co[((2 * p) * N + i) * N + j] = (double)v.x;
+            co[((2 * p + 1) * N + i) * N + j] = (double)v.y;
           }
         });
   }
@@ -390,61 +412,69 @@ __global__ void __launch_bounds__(kThreads) k_assemble(const double2* wfine, con
 
 }  // namespace
 
-template <int n>
+template <int n, class T>
 size_t smem_bytes() {
-  return (size_t)(n + Chunk<n>::SMEM_ELEMS) * sizeof(double2);
+  using C2 = typename Vec2Of<T>::type;
+  return (size_t)(n + Chunk<n, sizeof(C2)>::SMEM_ELEMS) * sizeof(C2);
 }
 
-template <int n>
+template <int n, class T>
 void set_smem_attributes() {
   static bool done = false;
   if (done) return;
-  const int sm = (int)smem_bytes<n>();
-  cudaFuncSetAttribute(k_prep<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_i1<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_i24<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_i3<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_assemble<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  const int sm = (int)smem_bytes<n, T>();
+  cudaFuncSetAttribute(k_prep<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i1<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i24<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i3<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_assemble<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   done = true;
 }
 
-template <int n>
+template <int n, class T>
 int i3_blocks_per_sm() {
-  set_smem_attributes<n>();
+  set_smem_attributes<n, T>();
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n>, kThreads, smem_bytes<n>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n, T>, kThreads, smem_bytes<n, T>());
   return b < 1 ? 1 : b;
 }
 
-template <int n>
+template <int n, class T>
 cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells,
                             cudaStream_t s, long long& launches, KernelTimer* tm) {
-  set_smem_attributes<n>();
-  const size_t sm = smem_bytes<n>();
+  using C2 = typename Vec2Of<T>::type;
+  set_smem_attributes<n, T>();
+  const TabPtrs<T> tb = tab_ptrs<T>(t);
+  C2* what = (C2*)cw.what;
+  C2* wfine = (C2*)cw.wfine;
+  C2* Dacc = (C2*)cw.Dacc;
+  T* K2acc = (T*)cw.K2acc;
+  C2* K4acc = (C2*)cw.K4acc;
+  C2* K3part = (C2*)cw.K3part;
+  C2* ws = (C2*)cw.ws;
+  const size_t sm = smem_bytes<n, T>();
   auto begin = [&](int g) { if (tm) tm->begin(g, s); };
   auto end = [&]() { if (tm) tm->end(s); };
   begin(KG_PREP);
-  k_prep<n><<<ncells, kThreads, sm, s>>>(w, cw.what, cw.wfine, cw.ws, t.tw);
+  k_prep<n, T><<<ncells, kThreads, sm, s>>>(w, what, wfine, ws, tb.tw);
   end();
   begin(KG_I1);
-  k_i1<n><<<ncells, kThreads, sm, s>>>(cw.what, cw.wfine, cw.Dacc, cw.ws, t.tw, t.phip, t.Ktab, t.J);
+  k_i1<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, Dacc, ws, tb.tw, tb.phip, tb.Ktab, t.J);
   end();
   begin(KG_I24);
-  k_i24<n><<<ncells, kThreads, sm, s>>>(cw.what, cw.wfine, cw.K2acc, cw.K4acc, cw.ws, t.tw, t.psi, t.J);
+  k_i24<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, K2acc, K4acc, ws, tb.tw, tb.psi, t.J);
   end();
   const int nunits = ncells * t.J * cw.nmc;
   const int grid = nunits < cw.grid_i3 ? nunits : cw.grid_i3;
   begin(KG_I3);
-  k_i3<n><<<grid, kThreads, sm, s>>>(cw.what, cw.wfine, cw.K3part, cw.ws, t.tw, t.psip_s, t.phase, t.J, t.M,
-                                     cw.nmc, cw.mch, nunits);
+  k_i3<n, T><<<grid, kThreads, sm, s>>>(what, wfine, K3part, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M, cw.nmc,
+                                        cw.mch, nunits);
   end();
   begin(KG_ASSEMBLE);
-  k_assemble<n><<<ncells, kThreads, sm, s>>>(cw.wfine, cw.Dacc, cw.K2acc, cw.K4acc, cw.K3part, t.J * cw.nmc,
-                                             cw.ws, t.tw, c);
+  k_assemble<n, T><<<ncells, kThreads, sm, s>>>(wfine, Dacc, K2acc, K4acc, K3part, t.J * cw.nmc, ws, tb.tw, c);
   end();
   launches += 5;
   return cudaGetLastError();
 }
-
 
 }  // namespace qbe

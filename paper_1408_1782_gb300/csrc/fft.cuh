@@ -39,13 +39,35 @@ __host__ __device__ __forceinline__ int pos_of_freq(int k) {
   return B * (k % A) + k / A;
 }
 
+// Real type of a complex vector type, and fused multiply-add per precision.
+template <class C2> struct RealOf;
+template <> struct RealOf<double2> { using type = double; };
+template <> struct RealOf<float2> { using type = float; };
+template <class T> struct Vec2Of;
+template <> struct Vec2Of<double> { using type = double2; };
+template <> struct Vec2Of<float> { using type = float2; };
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double2 mk2(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 mk2(float x, float y) { return make_float2(x, y); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaT(a.x, b.x, -a.y * b.y), fmaT(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaT(a.x, b.x, a.y * b.y), fmaT(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+  return make_double2(fmaT(a.x, b.x, -a.y * b.y), fmaT(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
-  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+  return make_double2(fmaT(a.x, b.x, a.y * b.y), fmaT(a.y, b.x, -a.x * b.y));
 }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
@@ -62,15 +84,16 @@ __host__ __device__ constexpr double cos16(int k) {
 __host__ __device__ constexpr double sin16(int k) { return cos16(k - 4); }
 
 // x * exp(SIGN * 2 pi i k / R) for R <= 16, k a compile-time constant after unrolling.
-template <int R, int SIGN>
-__device__ __forceinline__ double2 twid(int k, double2 x) {
+template <int R, int SIGN, class C2>
+__device__ __forceinline__ C2 twid(int k, C2 x) {
+  using T = typename RealOf<C2>::type;
   const int k16 = (k * (16 / R)) & 15;
   if (k16 == 0) return x;
-  if (k16 == 8) return make_double2(-x.x, -x.y);
-  if (k16 == 4) return SIGN > 0 ? make_double2(-x.y, x.x) : make_double2(x.y, -x.x);
-  if (k16 == 12) return SIGN > 0 ? make_double2(x.y, -x.x) : make_double2(-x.y, x.x);
-  const double c = cos16(k16), s = SIGN * sin16(k16);
-  return make_double2(fma(x.x, c, -x.y * s), fma(x.x, s, x.y * c));
+  if (k16 == 8) return mk2(-x.x, -x.y);
+  if (k16 == 4) return SIGN > 0 ? mk2(-x.y, x.x) : mk2(x.y, -x.x);
+  if (k16 == 12) return SIGN > 0 ? mk2(x.y, -x.x) : mk2(-x.y, x.x);
+  const T c = (T)cos16(k16), s = (T)(SIGN * sin16(k16));
+  return mk2(fmaT(x.x, c, -x.y * s), fmaT(x.x, s, x.y * c));
 }
 
 __host__ __device__ constexpr int ilog2c(int r) { return r <= 1 ? 0 : 1 + ilog2c(r / 2); }
@@ -83,46 +106,47 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
 // Butterflies with a non-trivial twiddle w = c + i s use the cosine-factored
 // form (u +- w x) = u +- c (x + (s/c) i x): six FMAs instead of two products,
 // two FMAs and four additions (|s/c| <= tan(3 pi/8) for R <= 16).
-template <int R, int SIGN, int S>
+template <int R, int SIGN, int S, class C2>
 struct DftStage {
-  __device__ __forceinline__ static void run(double2 (&b)[R]) {
+  __device__ __forceinline__ static void run(C2 (&b)[R]) {
+    using T = typename RealOf<C2>::type;
 #pragma unroll
     for (int g = 0; g < R; g += S) {
 #pragma unroll
       for (int k = 0; k < S / 2; ++k) {
         const int k16 = (k * (16 / S)) & 15;
-        const double2 u = b[g + k];
-        const double2 x = b[g + k + S / 2];
+        const C2 u = b[g + k];
+        const C2 x = b[g + k + S / 2];
         if ((k16 & 3) == 0) {
-          const double2 t = twid<16, SIGN>(k16, x);
+          const C2 t = twid<16, SIGN>(k16, x);
           b[g + k] = cadd(u, t);
           b[g + k + S / 2] = csub(u, t);
         } else {
-          const double c = cos16(k16);
-          const double r = (SIGN * sin16(k16)) / c;
-          const double qx = fma(-r, x.y, x.x);
-          const double qy = fma(r, x.x, x.y);
-          b[g + k] = make_double2(fma(c, qx, u.x), fma(c, qy, u.y));
-          b[g + k + S / 2] = make_double2(fma(-c, qx, u.x), fma(-c, qy, u.y));
+          const T c = (T)cos16(k16);
+          const T r = (T)((SIGN * sin16(k16)) / cos16(k16));
+          const T qx = fmaT(-r, x.y, x.x);
+          const T qy = fmaT(r, x.x, x.y);
+          b[g + k] = mk2(fmaT(c, qx, u.x), fmaT(c, qy, u.y));
+          b[g + k + S / 2] = mk2(fmaT(-c, qx, u.x), fmaT(-c, qy, u.y));
         }
       }
     }
-    DftStage<R, SIGN, 2 * S>::run(b);
+    DftStage<R, SIGN, 2 * S, C2>::run(b);
   }
 };
-template <int R, int SIGN>
-struct DftStage<R, SIGN, 2 * R> {
-  __device__ __forceinline__ static void run(double2 (&)[R]) {}
+template <int R, int SIGN, class C2>
+struct DftStage<R, SIGN, 2 * R, C2> {
+  __device__ __forceinline__ static void run(C2 (&)[R]) {}
 };
 
 // In-register DFT of length R <= 16 (natural order in and out).
-template <int R, int SIGN>
-__device__ __forceinline__ void dft(double2 (&a)[R]) {
+template <int R, int SIGN, class C2>
+__device__ __forceinline__ void dft(C2 (&a)[R]) {
   constexpr int L2 = ilog2c(R);
-  double2 b[R];
+  C2 b[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) b[i] = a[bitrev(i, L2)];
-  DftStage<R, SIGN, 2>::run(b);
+  DftStage<R, SIGN, 2, C2>::run(b);
 #pragma unroll
   for (int i = 0; i < R; ++i) a[i] = b[i];
 }
@@ -131,15 +155,15 @@ __device__ __forceinline__ void dft(double2 (&a)[R]) {
 // element e of line l at buf[l*ls + e*es].  tw[t2*A + k1] = exp(-2 pi i t2 k1 / n).
 // SIGN < 0: forward, natural -> permuted.  SIGN > 0: inverse, permuted -> natural.
 // Must be called by every thread of the block; ends with __syncthreads().
-template <int n, int SIGN>
-__device__ __forceinline__ void fft_lines(double2* buf, int nl, int ls, int es, const double2* __restrict__ tw) {
+template <int n, int SIGN, class C2>
+__device__ __forceinline__ void fft_lines(C2* buf, int nl, int ls, int es, const C2* __restrict__ tw) {
   constexpr int A = Split<n>::A, B = Split<n>::B;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (SIGN < 0) {
     for (int task = tid; task < nl * B; task += nt) {
       const int l = task % nl, t2 = task / nl;
-      double2* base = buf + l * ls + t2 * es;
-      double2 a[A];
+      C2* base = buf + l * ls + t2 * es;
+      C2 a[A];
 #pragma unroll
       for (int t1 = 0; t1 < A; ++t1) a[t1] = base[B * t1 * es];
       dft<A, -1>(a);
@@ -151,8 +175,8 @@ __device__ __forceinline__ void fft_lines(double2* buf, int nl, int ls, int es, 
     __syncthreads();
     for (int task = tid; task < nl * A; task += nt) {
       const int l = task % nl, k1 = task / nl;
-      double2* base = buf + l * ls + B * k1 * es;
-      double2 b[B];
+      C2* base = buf + l * ls + B * k1 * es;
+      C2 b[B];
 #pragma unroll
       for (int t2 = 0; t2 < B; ++t2) b[t2] = base[t2 * es];
       dft<B, -1>(b);
@@ -163,8 +187,8 @@ __device__ __forceinline__ void fft_lines(double2* buf, int nl, int ls, int es, 
   } else {
     for (int task = tid; task < nl * A; task += nt) {
       const int l = task % nl, k1 = task / nl;
-      double2* base = buf + l * ls + B * k1 * es;
-      double2 b[B];
+      C2* base = buf + l * ls + B * k1 * es;
+      C2 b[B];
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2) b[k2] = base[k2 * es];
       dft<B, 1>(b);
@@ -174,8 +198,8 @@ __device__ __forceinline__ void fft_lines(double2* buf, int nl, int ls, int es, 
     __syncthreads();
     for (int task = tid; task < nl * B; task += nt) {
       const int l = task % nl, t2 = task / nl;
-      double2* base = buf + l * ls + t2 * es;
-      double2 a[A];
+      C2* base = buf + l * ls + t2 * es;
+      C2 a[A];
 #pragma unroll
       for (int k1 = 0; k1 < A; ++k1) a[k1] = base[B * k1 * es];
 #pragma unroll
@@ -192,15 +216,14 @@ __device__ __forceinline__ void fft_lines(double2* buf, int nl, int ls, int es, 
 // spectral value by mul(line, pos) (pos = permuted position), inverse FFT.  The
 // second forward stage, the multiplication and the first inverse stage act on
 // the same B contiguous values, so they are fused in registers.
-template <int n, class MUL>
-__device__ __forceinline__ void fft_conv_lines(double2* buf, int nl, int ls, int es, const double2* __restrict__ tw,
-                                               MUL mul) {
+template <int n, class C2, class MUL>
+__device__ __forceinline__ void fft_conv_lines(C2* buf, int nl, int ls, int es, const C2* __restrict__ tw, MUL mul) {
   constexpr int A = Split<n>::A, B = Split<n>::B;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int task = tid; task < nl * B; task += nt) {
     const int l = task % nl, t2 = task / nl;
-    double2* base = buf + l * ls + t2 * es;
-    double2 a[A];
+    C2* base = buf + l * ls + t2 * es;
+    C2 a[A];
 #pragma unroll
     for (int t1 = 0; t1 < A; ++t1) a[t1] = base[B * t1 * es];
     dft<A, -1>(a);
@@ -212,13 +235,13 @@ __device__ __forceinline__ void fft_conv_lines(double2* buf, int nl, int ls, int
   __syncthreads();
   for (int task = tid; task < nl * A; task += nt) {
     const int l = task % nl, k1 = task / nl;
-    double2* base = buf + l * ls + B * k1 * es;
-    double2 b[B];
+    C2* base = buf + l * ls + B * k1 * es;
+    C2 b[B];
 #pragma unroll
     for (int t2 = 0; t2 < B; ++t2) b[t2] = base[t2 * es];
     dft<B, -1>(b);
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) b[k2] = cscale(b[k2], mul(l, B * k1 + k2));
+    for (int k2 = 0; k2 < B; ++k2) b[k2] = cscale(b[k2], (typename RealOf<C2>::type)mul(l, B * k1 + k2));
     dft<B, 1>(b);
 #pragma unroll
     for (int t2 = 0; t2 < B; ++t2) base[t2 * es] = b[t2];
@@ -226,8 +249,8 @@ __device__ __forceinline__ void fft_conv_lines(double2* buf, int nl, int ls, int
   __syncthreads();
   for (int task = tid; task < nl * B; task += nt) {
     const int l = task % nl, t2 = task / nl;
-    double2* base = buf + l * ls + t2 * es;
-    double2 a[A];
+    C2* base = buf + l * ls + t2 * es;
+    C2 a[A];
 #pragma unroll
     for (int k1 = 0; k1 < A; ++k1) a[k1] = base[B * k1 * es];
 #pragma unroll
@@ -242,8 +265,9 @@ __device__ __forceinline__ void fft_conv_lines(double2* buf, int nl, int ls, int
 // Chunk sizes (rows per row-pass chunk, columns per column-pass chunk) so that a
 // chunk of complex doubles occupies about 64 KB of shared memory (three blocks
 // per SM fit) and the radix-B stage has at least one task per thread.
-template <int n> struct Chunk {
-  static constexpr int RC = (n >= 256) ? 16 : (n >= 128) ? 32 : n;
+template <int n, int ELEM = 16> struct Chunk {
+  static constexpr int RC0 = 65536 / (n * ELEM);
+  static constexpr int RC = RC0 >= n ? n : RC0;
   static constexpr int CC = RC;
   static constexpr int LS = n + 1;                 // padded row stride (odd => no bank conflicts)
   static constexpr int SMEM_ELEMS = (RC * LS > CC * n ? RC * LS : CC * n);
@@ -252,9 +276,9 @@ template <int n> struct Chunk {
 // Row pass over an n x n field (rows = fixed ix, transform along iy):
 // for each chunk: sm[r][iy] = ld(ix, iy); [FFT DIR1]; [sm = mid(ix, iy, sm)]; [FFT DIR2]; st(ix, iy, sm).
 // DIR = 0 skips that transform; HAS_MID selects the pointwise middle step.
-template <int n, int DIR1, bool HAS_MID, int DIR2, class LD, class MID, class ST>
-__device__ __forceinline__ void row_pass(double2* sm, const double2* tw, LD ld, MID mid, ST st) {
-  constexpr int RC = Chunk<n>::RC, LS = Chunk<n>::LS;
+template <int n, int DIR1, bool HAS_MID, int DIR2, class C2, class LD, class MID, class ST>
+__device__ __forceinline__ void row_pass(C2* sm, const C2* tw, LD ld, MID mid, ST st) {
+  constexpr int RC = Chunk<n, sizeof(C2)>::RC, LS = Chunk<n, sizeof(C2)>::LS;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int r0 = 0; r0 < n; r0 += RC) {
     for (int idx = tid; idx < RC * n; idx += nt) {
@@ -280,9 +304,9 @@ __device__ __forceinline__ void row_pass(double2* sm, const double2* tw, LD ld, 
 }
 
 // Column pass (transform along ix) over chunks of CC columns held as sm[ix][c].
-template <int n, int DIR1, bool HAS_MID, int DIR2, class LD, class MID, class ST>
-__device__ __forceinline__ void col_pass(double2* sm, const double2* tw, LD ld, MID mid, ST st) {
-  constexpr int CC = Chunk<n>::CC;
+template <int n, int DIR1, bool HAS_MID, int DIR2, class C2, class LD, class MID, class ST>
+__device__ __forceinline__ void col_pass(C2* sm, const C2* tw, LD ld, MID mid, ST st) {
+  constexpr int CC = Chunk<n, sizeof(C2)>::CC;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < n; c0 += CC) {
     for (int idx = tid; idx < CC * n; idx += nt) {
@@ -309,9 +333,9 @@ __device__ __forceinline__ void col_pass(double2* sm, const double2* tw, LD ld, 
 
 // Column pass doing a circular convolution along ix for each column iy:
 // sm[ix][c] = ld(ix, iy); forward FFT; times mul(pos_x, iy); inverse FFT; st(ix, iy, value).
-template <int n, class LD, class MUL, class ST>
-__device__ __forceinline__ void col_conv_pass(double2* sm, const double2* tw, LD ld, MUL mul, ST st) {
-  constexpr int CC = Chunk<n>::CC;
+template <int n, class C2, class LD, class MUL, class ST>
+__device__ __forceinline__ void col_conv_pass(C2* sm, const C2* tw, LD ld, MUL mul, ST st) {
+  constexpr int CC = Chunk<n, sizeof(C2)>::CC;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < n; c0 += CC) {
     for (int idx = tid; idx < CC * n; idx += nt) {
@@ -329,10 +353,10 @@ __device__ __forceinline__ void col_conv_pass(double2* sm, const double2* tw, LD
 }
 
 // Column pass over a subset of columns cols[0..ncols) (chunks of CC columns).
-template <int n, int DIR1, bool HAS_MID, int DIR2, class LD, class MID, class ST>
-__device__ __forceinline__ void col_pass_list(double2* sm, const double2* tw, const int* cols, int ncols, LD ld,
-                                              MID mid, ST st) {
-  constexpr int CC = Chunk<n>::CC;
+template <int n, int DIR1, bool HAS_MID, int DIR2, class C2, class LD, class MID, class ST>
+__device__ __forceinline__ void col_pass_list(C2* sm, const C2* tw, const int* cols, int ncols, LD ld, MID mid,
+                                              ST st) {
+  constexpr int CC = Chunk<n, sizeof(C2)>::CC;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < ncols; c0 += CC) {
     const int nc = (ncols - c0) < CC ? (ncols - c0) : CC;
@@ -359,12 +383,13 @@ __device__ __forceinline__ void col_pass_list(double2* sm, const double2* tw, co
 }
 
 struct NoMid {
-  __device__ double2 operator()(int, int, double2 v) const { return v; }
+  template <class C2>
+  __device__ C2 operator()(int, int, C2 v) const { return v; }
 };
 
 // Load the n-point twiddle table into shared memory.
-template <int n>
-__device__ __forceinline__ void load_twiddles(double2* sm_tw, const double2* __restrict__ g_tw) {
+template <int n, class C2>
+__device__ __forceinline__ void load_twiddles(C2* sm_tw, const C2* __restrict__ g_tw) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) sm_tw[i] = g_tw[i];
   __syncthreads();
 }

@@ -21,21 +21,48 @@ struct Tables {
   double* psi = nullptr;        // [J][n*n] psi_R(sigma . theta_j)                        (eq. approxH-J)
   double* psip_s = nullptr;     // [J][n*n] psi_R(sigma . theta_j^perp) / n^2              (eq. approxH-J)
   double2* phase = nullptr;     // [J*M][2][n] sqrt(pi w_m / J) e^{i alpha_x sigma_x}, e^{i alpha_y sigma_y} (eq. approxH-JM)
+  // FP32 copies of the same tables (FP32-split form only; null otherwise)
+  float2* tw_f = nullptr;
+  float* phip_f = nullptr;
+  float* Ktab_f = nullptr;
+  float* psi_f = nullptr;
+  float* psip_s_f = nullptr;
+  float2* phase_f = nullptr;
 };
+
+// Typed view of the tables for the transform precision T.
+template <class T> struct TabPtrs;
+template <> struct TabPtrs<double> {
+  const double2* tw; const double* phip; const double* Ktab; const double* psi; const double* psip_s;
+  const double2* phase;
+};
+template <> struct TabPtrs<float> {
+  const float2* tw; const float* phip; const float* Ktab; const float* psi; const float* psip_s;
+  const float2* phase;
+};
+template <class T> TabPtrs<T> tab_ptrs(const Tables& t);
+template <> inline TabPtrs<double> tab_ptrs<double>(const Tables& t) {
+  return {t.tw, t.phip, t.Ktab, t.psi, t.psip_s, t.phase};
+}
+template <> inline TabPtrs<float> tab_ptrs<float>(const Tables& t) {
+  return {t.tw_f, t.phip_f, t.Ktab_f, t.psi_f, t.psip_s_f, t.phase_f};
+}
 
 // Per-evaluation buffers of the collision operator for a batch of nb cells.
 struct CollisionWork {
+  int prec = 0;        // 0: FP64 transforms, 1: FP32 transforms (FP32-split form)
   int nb = 0;          // cells per batch
   int nmc = 1;         // m-chunks per (cell, j) unit of the I3 kernel
   int mch = 1;         // m values per chunk
   int grid_i3 = 0;     // persistent grid of the I3 kernel
-  double2* what = nullptr;   // [nb][4][n*n] spectral pairs (w0+iw1, w2+iw3, w1+iw2, w3)
-  double2* wfine = nullptr;  // [nb][2][n*n] fine-grid fields (w0+iw1, w2+iw3)
-  double2* Dacc = nullptr;   // [nb][2][n*n] spectral D (pairs (1,2), (3,-))
-  double* K2acc = nullptr;   // [nb][n*n]
-  double2* K4acc = nullptr;  // [nb][2][n*n] spectral K4 pairs (0,1), (2,3)
-  double2* K3part = nullptr; // [nb*J*nmc][2][n*n] fine-grid K3 pair partial sums
-  double2* ws = nullptr;     // per-CTA scratch
+  // buffers of the transform precision (complex = double2 or float2)
+  void* what = nullptr;      // [nb][4][n*n] spectral pairs (w0+iw1, w2+iw3, w1+iw2, w3)
+  void* wfine = nullptr;     // [nb][2][n*n] fine-grid fields (w0+iw1, w2+iw3)
+  void* Dacc = nullptr;      // [nb][2][n*n] spectral D (pairs (1,2), (3,-))
+  void* K2acc = nullptr;     // [nb][n*n] (real)
+  void* K4acc = nullptr;     // [nb][2][n*n] spectral K4 pairs (0,1), (2,3)
+  void* K3part = nullptr;    // [nb*J*nmc][2][n*n] fine-grid K3 pair partial sums
+  void* ws = nullptr;        // per-CTA scratch
   size_t ws_fields = 0;      // complex n*n fields of scratch per CTA slot
   int ws_slots = 0;          // number of CTA slots in ws
   double* cbuf = nullptr;    // [nb][4][N][N] staging for collide in/out
@@ -96,8 +123,8 @@ struct KernelTimer {
   }
 };
 
-// Host-side table construction (tables.cpp).
-bool build_tables(int N, int J, int M, double L, double R, Tables& t, std::string& err);
+// Host-side table construction (tables.cpp); with_f32 also uploads FP32 copies.
+bool build_tables(int N, int J, int M, double L, double R, Tables& t, std::string& err, bool with_f32 = false);
 void free_tables(Tables& t);
 
 // Wall Fermi-Dirac state in Pauli form on the coarse grid [4][N][N] (eq. W_FermiDirac).
@@ -106,11 +133,11 @@ void fermi_dirac_pauli(const qbe_fd& fd, int N, double L, std::vector<double>& o
 // Collision operator on a batch (collision.cu).  w, c: device [nb][4][N][N].
 cudaError_t collide_batch(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells,
                           cudaStream_t s, long long& launches, KernelTimer* tm);
-cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw);
-template <int n>
+cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int prec = 0);
+template <int n, class T>
 cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells, cudaStream_t s,
                             long long& launches, KernelTimer* tm);
-template <int n>
+template <int n, class T>
 int i3_blocks_per_sm();
 void free_collision_work(CollisionWork& cw);
 

@@ -113,7 +113,7 @@ int qbe_create(const qbe_grid* g, qbe_handle** out) {
   if (!n_ok || g->Nx < 1 || g->J < 2 || g->J > 64 || (g->J % 2) != 0 || g->M < 1 || g->M > 64 ||
       !(g->L > 0) || !(g->R > 0) || !std::isfinite(g->L) || !std::isfinite(g->R))
     return QBE_ERR_ARG;
-  if (g->precision != 0) return QBE_ERR_UNSUPPORTED;
+  if (g->precision != 0 && g->precision != 1) return QBE_ERR_UNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || g->device < 0 || g->device >= ndev) return QBE_ERR_CUDA;
   qbe_handle* h = new (std::nothrow) qbe_handle();
@@ -121,12 +121,12 @@ int qbe_create(const qbe_grid* g, qbe_handle** out) {
   h->g = *g;
   DeviceGuard dg(g->device);
   std::string err;
-  if (!build_tables(g->N, g->J, g->M, g->L, g->R, h->tab, err)) {
+  if (!build_tables(g->N, g->J, g->M, g->L, g->R, h->tab, err, g->precision == 1)) {
     qbe_destroy(h);
     return QBE_ERR_ALLOC;
   }
   // collision batch: all cells of the state (one evaluation per RK stage)
-  if (alloc_collision_work(h->tab, g->Nx, h->cw) != cudaSuccess) {
+  if (alloc_collision_work(h->tab, g->Nx, h->cw, g->precision) != cudaSuccess) {
     qbe_destroy(h);
     return QBE_ERR_ALLOC;
   }

@@ -88,7 +88,22 @@ bool upload(T*& dst, const std::vector<T>& src, std::string& err) {
 
 }  // namespace
 
-bool build_tables(int N, int J, int M, double L, double R, Tables& t, std::string& err) {
+template <class D, class S>
+std::vector<D> to_f32(const std::vector<S>& v);
+template <>
+std::vector<float> to_f32<float, double>(const std::vector<double>& v) {
+  std::vector<float> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+  return o;
+}
+template <>
+std::vector<float2> to_f32<float2, double2>(const std::vector<double2>& v) {
+  std::vector<float2> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+  return o;
+}
+
+bool build_tables(int N, int J, int M, double L, double R, Tables& t, std::string& err, bool with_f32) {
   const int n = 2 * N;
   int A = 0, B = 0;
   split_of(n, A, B);
@@ -161,12 +176,20 @@ bool build_tables(int N, int J, int M, double L, double R, Tables& t, std::strin
       }
     }
 
-  return upload(t.tw, tw, err) && upload(t.phip, phip, err) && upload(t.Ktab, Ktab, err) &&
-         upload(t.psi, psi, err) && upload(t.psip_s, psip, err) && upload(t.phase, phase, err);
+  bool ok = upload(t.tw, tw, err) && upload(t.phip, phip, err) && upload(t.Ktab, Ktab, err) &&
+            upload(t.psi, psi, err) && upload(t.psip_s, psip, err) && upload(t.phase, phase, err);
+  if (ok && with_f32) {
+    ok = upload(t.tw_f, to_f32<float2>(tw), err) && upload(t.phip_f, to_f32<float>(phip), err) &&
+         upload(t.Ktab_f, to_f32<float>(Ktab), err) && upload(t.psi_f, to_f32<float>(psi), err) &&
+         upload(t.psip_s_f, to_f32<float>(psip), err) && upload(t.phase_f, to_f32<float2>(phase), err);
+  }
+  return ok;
 }
 
 void free_tables(Tables& t) {
   cudaFree(t.tw); cudaFree(t.phip); cudaFree(t.Ktab); cudaFree(t.psi); cudaFree(t.psip_s); cudaFree(t.phase);
+  cudaFree(t.tw_f); cudaFree(t.phip_f); cudaFree(t.Ktab_f); cudaFree(t.psi_f); cudaFree(t.psip_s_f);
+  cudaFree(t.phase_f);
   t = Tables();
 }
 

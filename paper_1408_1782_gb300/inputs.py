@@ -203,11 +203,11 @@ def bandlimited_w(N: int, band: int, ncells: int = 1, seed: int = 0, scale: floa
 # Sec. 5) and the benchmark configurations.
 WORKLOADS = {
     "plain_fp64_n16": dict(N=16, Nx=16, L=12.0, R=7.5, J=32, M=32, bc="periodic",
-                           B=(0.0, 0.0, 0.0), dt=0.01, steps=10, perturb=0.0),
+                           B=(0.0, 0.0, 0.0), dt=0.01, steps=10, perturb=0.0, precision=0),
     "plain_fp64_n64": dict(N=64, Nx=128, L=12.0, R=7.5, J=32, M=32, bc="dirichlet",
                            wall=dict(beta=1.0, mu_up=0.0, mu_dn=0.0),
-                           B=(0.0, 0.0, 0.5), dt=0.005, steps=1000, perturb=0.05),
+                           B=(0.0, 0.0, 0.5), dt=0.005, steps=1000, perturb=0.05, precision=0),
     "precision_n128": dict(N=128, Nx=256, L=12.0, R=7.5, J=32, M=32, bc="maxwell", alpha=0.5,
                            wall=dict(beta=1.0, mu_up=0.0, mu_dn=0.0),
-                           B=(0.3, 0.0, 0.4), dt=0.002, steps=200, perturb=0.05),
+                           B=(0.3, 0.0, 0.4), dt=0.002, steps=200, perturb=0.05, precision=1),
 }

@@ -130,9 +130,11 @@ def collide_noalloc(w, out, J=32, M=32, L=12.0, R=7.5, stream=None):
 class Solver:
     """One simulation on one GPU (see include/qbe.h for the semantics of each call)."""
 
-    def __init__(self, N, Nx, J=32, M=32, L=12.0, R=7.5, device=0, stream=None):
+    def __init__(self, N, Nx, J=32, M=32, L=12.0, R=7.5, device=0, stream=None, precision=0):
+        """precision 0: plain FP64; 1: FP32-split (collision transforms in FP32, the rest in FP64)."""
         self.N, self.Nx, self.J, self.M, self.L, self.R = N, Nx, J, M, L, R
-        g = QbeGrid(N, Nx, J, M, L, R, 0, device)
+        self.precision = precision
+        g = QbeGrid(N, Nx, J, M, L, R, precision, device)
         h = _c_void_p()
         rc = lib().qbe_create(ctypes.byref(g), ctypes.byref(h))
         if rc != 0:

@@ -11,7 +11,12 @@ applied to the seeded synthetic inputs; nothing comes from the CUDA library.
                        Dirichlet workload's initial state (5% perturbation) and
                        their collision operator C[W].
 
-Usage: python tests/golden/make_golden.py [n16|n64|all]
+  precision_n128_cells.npz
+                       N=128, J=M=32: two cells (0 and 131) of the 256-cell
+                       Maxwell workload's initial state (5% perturbation) and
+                       their C[W] (the FP32-split form is checked against it).
+
+Usage: python tests/golden/make_golden.py [n16|n64|n128|all]
 """
 import os
 import sys
@@ -59,9 +64,25 @@ def make_n64():
     np.savez_compressed(os.path.join(HERE, "plain_fp64_n64_cells.npz"), cells=cells, W=W[cells], C=C)
 
 
+def make_n128():
+    import multiprocessing as mp
+
+    wl = inputs.WORKLOADS["precision_n128"]
+    p = O.Params(N=wl["N"], L=wl["L"], R=wl["R"], J=wl["J"], M=wl["M"])
+    W = inputs.synthetic_w(wl["N"], wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])
+    cells = np.array([0, 131])
+    t = time.time()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        C = O.collision(W[cells], p, mapper=lambda f, it: pool.map(f, list(it), chunksize=1))
+    print(f"n128 cells {time.time() - t:.1f}s", flush=True)
+    np.savez_compressed(os.path.join(HERE, "precision_n128_cells.npz"), cells=cells, W=W[cells], C=C)
+
+
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "all"
     if which in ("n64", "all"):
         make_n64()
     if which in ("n16", "all"):
         make_n16()
+    if which in ("n128", "all"):
+        make_n128()

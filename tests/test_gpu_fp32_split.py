@@ -1,0 +1,113 @@
+"""FP32-split precision form against the FP64 oracle and the FP64 GPU form.
+
+The collision operator's transforms, products and per-unit accumulations run
+in FP32; its input/output, the reduction of its per-unit partial sums, the
+transport with its boundary projections, the RK2 accumulation and the moments
+stay FP64.  Stated tolerances for C[W] (measured values on a GB300 in
+parentheses): max |dC| <= 5e-6 max |C| (5e-7 to 1e-6), and in the paper's
+error norm, the sum over Pauli components of relative L1 errors (Fig. 1
+caption), <= 5e-5 (0.8e-5 to 1.2e-5).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import qbe_oracle as O
+from paper_1408_1782_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_MAX = 5e-6
+TOL_L1 = 5e-5
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def qbe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1408_1782_gb300 import qbe as q
+
+    return q
+
+
+def errors(got, ref):
+    mx = np.abs(got - ref).max() / np.abs(ref).max()
+    l1 = max(sum(np.abs(got[c, k] - ref[c, k]).sum() / np.abs(ref[c, k]).sum() for k in range(4))
+             for c in range(got.shape[0]))
+    return mx, l1
+
+
+def collide(q, w, N, J, M, precision):
+    import torch
+
+    s = q.Solver(N, w.shape[0], J=J, M=M, stream=torch.cuda.current_stream(), precision=precision)
+    c = s.collide(torch.from_numpy(np.ascontiguousarray(w)).cuda())
+    torch.cuda.synchronize()
+    out = c.cpu().numpy()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("N,J,M,ncells", [(16, 32, 32, 2), (32, 8, 8, 3), (8, 4, 4, 5)])
+def test_fp32_split_collision_against_oracle(qbe, N, J, M, ncells):
+    w = inputs.synthetic_w(N, ncells, seed=3 + N, perturb=0.05)
+    ref = O.collision(w, O.Params(N=N, J=J, M=M))
+    mx, l1 = errors(collide(qbe, w, N, J, M, 1), ref)
+    assert mx < TOL_MAX and l1 < TOL_L1, (mx, l1)
+
+
+@pytest.mark.parametrize("name", ["plain_fp64_n64_cells.npz", "precision_n128_cells.npz"])
+def test_fp32_split_collision_on_stored_oracle_cells(qbe, name):
+    """N = 64 and N = 128 cells of the at-scale workloads (J = M = 32)."""
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    g = np.load(path)
+    N = g["W"].shape[-1]
+    mx, l1 = errors(collide(qbe, g["W"], N, 32, 32, 1), g["C"])
+    assert mx < TOL_MAX and l1 < TOL_L1, (mx, l1)
+
+
+def test_fp32_split_matches_fp64_gpu_form_on_all_cells(qbe):
+    """All 128 cells of the N = 64 Dirichlet workload, against the plain FP64 GPU form."""
+    wl = inputs.WORKLOADS["plain_fp64_n64"]
+    W = inputs.synthetic_w(wl["N"], wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])
+    f64 = collide(qbe, W, 64, 32, 32, 0)
+    f32 = collide(qbe, W, 64, 32, 32, 1)
+    mx, l1 = errors(f32, f64)
+    assert mx < TOL_MAX and l1 < TOL_L1, (mx, l1)
+
+
+@pytest.mark.parametrize("bc", ["maxwell", "dirichlet"])
+def test_fp32_split_steps_against_oracle(qbe, bc):
+    """Two split steps with walls and a field: the state's change per step carries the C[W] tolerance,
+    the FP64 transport and RK update add nothing beyond round-off."""
+    import torch
+
+    N, Nx, J, M = 16, 5, 8, 8
+    W = inputs.synthetic_w(N, Nx, seed=9, perturb=0.05)
+    B = inputs.uniform_b(Nx, (0.3, 0.0, 0.4))
+    fd = (1.0, 0.0, 0.0, np.eye(2))
+    obc = O.Boundary(bc, fd, fd, alpha=0.5)
+    p = O.Params(N=N, J=J, M=M)
+    s = qbe.Solver(N, Nx, J=J, M=M, stream=torch.cuda.current_stream(), precision=1)
+    s.set_boundary(bc, qbe.fd_state(*fd), qbe.fd_state(*fd), alpha=0.5)
+    s.set_state(W)
+    s.set_bfield(B)
+    s.step(0.002, 2)
+    got = s.get_state()
+    ref = W
+    for _ in range(2):
+        ref = O.step(ref, B, 0.002, p, obc)
+    # relative to the change of the state over the two steps
+    assert np.abs(got - ref).max() < TOL_MAX * np.abs(ref - W).max() * 10
+    rho, mom, en = s.moments()
+    r2, m2, e2 = O.moments(ref, p)
+    assert np.abs(rho - r2).max() < 1e-7 * np.abs(r2).max()
+    s.close()
