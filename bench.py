@@ -41,6 +41,9 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (profiles/fp64_fp32_issue_rates.md)
 FP32_FMA_PER_CLK_PER_SM = 128        # measured 116 FFMA/clk/SM
+# DRAM bytes (read + write) per (cell, j, m) unit of k_i3 from one ncu capture of an 8-cell slice
+# (profiles/k_i3_f64_n64_8cells.md, profiles/k_i3_f32_n64_8cells.md), N = 64 only; scaled by units.
+I3_DRAM_BYTES_PER_UNIT = {(64, 0): 122.37e9 / 8192, (64, 1): 49.61e9 / 8192}
 
 
 def workload(name="plain_fp64_n64", precision=None):
@@ -217,6 +220,8 @@ def run_ours(args):
     g.build()
     from paper_1408_1782_gb300 import decomp, inputs, qbe
 
+    if args.workload == "batched_16":
+        return run_batched(args, local)
     wl = workload(args.workload, args.precision)
     if args.mode == "collide":
         return run_collide_only(args, wl, local)
@@ -320,7 +325,9 @@ def run_ours(args):
             "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)",
             "config": config_dict(wl, world),
             "roofline": {"kernel": "k_i3 (Hu-Ying I3 term)", "bound": "alu", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": (I3_DRAM_BYTES_PER_UNIT[(N, prec)] * Nx * wl["J"] * wl["M"]
+                                     if (N, prec) in I3_DRAM_BYTES_PER_UNIT else None),
                          "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_i3_s * 1e3,
                          "peak_source": (f"derived: {SM_COUNT} SMs x {lanes} {'FP64' if prec == 0 else 'FP32'} FMA/clk x 2 "
                                          f"flop x {sm_max:.0f} MHz (microbenchmark: DFMA 1.20 TFLOP/s, FFMA 73.1 "
@@ -385,6 +392,60 @@ def fp32_split_report(wl, W0, local, qbe, torch, np):
     return out
 
 
+def run_batched(args, local):
+    """16 independent simulations stepped with one CUDA graph launch per split step."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1408_1782_gb300 import inputs, qbe
+
+    rng = np.random.default_rng(0)
+    stream = torch.cuda.current_stream()
+    sims, desc = [], []
+    units = 0
+    for i in range(16):
+        N = int(rng.choice([32, 48, 64]))
+        Nx = int(rng.integers(16, 65))
+        bc = str(rng.choice(["periodic", "dirichlet", "maxwell"]))
+        B = rng.normal(size=3)
+        B *= rng.uniform(0, 1) / np.linalg.norm(B)
+        s = qbe.Solver(N, Nx, J=32, M=32, device=local, stream=stream, precision=1)
+        if bc != "periodic":
+            fd = qbe.fd_state(1.0, 0.0, 0.0)
+            s.set_boundary(bc, fd, fd, alpha=0.5)
+        s.set_bfield(inputs.uniform_b(Nx, B))
+        s.set_state(inputs.synthetic_w(N, Nx, seed=100 + i, perturb=0.05))
+        sims.append(s)
+        desc.append(f"{N}/{Nx}/{bc[0]}")
+        units += 2 * Nx * N * N
+    b = qbe.Batch(sims, stream=stream)
+    shapes = b.autotune()
+    dt = 0.005
+    b.step(dt, args.warmup)            # first call captures the graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    line = {"workload": "batched_16", "metric": "C[W] cell·k-pts/s", "value": units * args.steps / (t_ms * 1e-3),
+            "unit": "cell·k-pts/s", "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "dtype": "f32-split", "graph_launches_per_step": 1,
+            "sims": desc, "tuned_i3_shapes": [[gg, mm, round(ms, 3)] for gg, mm, ms in shapes],
+            "note": ("16 simulations drawn from the batching configuration's distributions with N in {32,48,64} "
+                     "and Nx in [16,64] (the full 64-simulation mix with N up to 128, Nx up to 256 needs about "
+                     "100 s per step on one GB300)")}
+    print(json.dumps(line), flush=True)
+    b.close()
+    for s in sims:
+        s.close()
+    return 0
+
+
 def run_collide_only(args, wl, local):
     """C[W] evaluations of the first `cells` cells of the workload's initial state."""
     import torch
@@ -431,7 +492,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["step", "collide"], default="step")
-    ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128"], default="plain_fp64_n64")
+    ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128", "batched_16"],
+                    default="plain_fp64_n64")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None)
     ap.add_argument("--cells", type=int, default=0)
     args = ap.parse_args()

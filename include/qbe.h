@@ -45,7 +45,7 @@ extern "C" {
 #define QBE_ERR_UNSUPPORTED (-5)  /* valid in the paper, not supported by this build */
 
 /* Discretisation (Sec. 3.2, Sec. 5): N velocity points per dimension (Fourier
- * cut-off, N in {8, 16, 32, 64, 128}); Nx finite volumes; J angular points on
+ * cut-off, N in {8, 16, 32, 48, 64, 96, 128}); Nx finite volumes; J angular points on
  * the half circle (eq. theta_grid; even, 2..64); M Gauss-Legendre radial nodes
  * (eq. approxH-JM; 1..64); L half-width of the periodised velocity box
  * [-L, L]^2; R truncation radius of the collision integrals (B_R).
@@ -164,6 +164,34 @@ long long qbe_launch_count(const qbe_handle* h);
 #define QBE_KG_RK 6
 int qbe_enable_timing(qbe_handle* h, int enable);
 int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launches);
+
+/* ------------------------------------------------------------------------
+ * Batches of independent simulations (SURVEY (f), batching form): several
+ * solver handles -- any mix of N, Nx, J, M, precision, boundary conditions and
+ * B fields, all on one device -- stepped together.  The first qbe_batch_step
+ * with a given dt captures one split step (Sec. 4) of every simulation into a
+ * CUDA graph, each simulation on its own branch so that independent
+ * simulations run concurrently; every step is then one graph launch.
+ * qbe_batch_autotune times, per simulation, the persistent grid (1..3 blocks
+ * per SM) and the number of m-chunks per (cell, angle) unit of the I3 kernel
+ * on the simulation's current state and keeps the fastest (it drops any
+ * captured graph).  Results are those of qbe_step on each handle, up to the
+ * summation order of the I3 partial sums that the tuned shape selects.
+ * The handles stay owned by the caller and must outlive the batch; each may
+ * appear once.  With a stream set (qbe_batch_set_stream) the steps are
+ * asynchronous on it; without one, qbe_batch_step synchronises before it
+ * returns.
+ * ------------------------------------------------------------------------ */
+typedef struct qbe_batch qbe_batch;
+int qbe_batch_create(qbe_handle* const* sims, int nsims, qbe_batch** out);
+void qbe_batch_destroy(qbe_batch* b);
+const char* qbe_batch_last_error(const qbe_batch* b);
+int qbe_batch_set_stream(qbe_batch* b, void* stream);
+int qbe_batch_autotune(qbe_batch* b);
+/* Tuned I3 launch shape of simulation `sim` (persistent grid, m-chunks) and
+ * the time of one collision evaluation with it (ms, 0 before autotuning). */
+int qbe_batch_tuned_shape(const qbe_batch* b, int sim, int* i3_grid, int* m_chunks, double* ms);
+int qbe_batch_step(qbe_batch* b, double dt, int nsteps);
 
 /* Collision operator without any memory allocation (the paper has no
  * counterpart: this is a deployment variant of qbe_collide).

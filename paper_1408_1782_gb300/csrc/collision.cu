@@ -13,6 +13,8 @@ cudaError_t collide_batch(const Tables& t, CollisionWork& cw, const double* w, d
       case 64: return collide_batch_n<64, float>(t, cw, w, c, ncells, s, launches, tm);
       case 128: return collide_batch_n<128, float>(t, cw, w, c, ncells, s, launches, tm);
       case 256: return collide_batch_n<256, float>(t, cw, w, c, ncells, s, launches, tm);
+    case 96: return collide_batch_n<96, float>(t, cw, w, c, ncells, s, launches, tm);
+    case 192: return collide_batch_n<192, float>(t, cw, w, c, ncells, s, launches, tm);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -22,6 +24,8 @@ cudaError_t collide_batch(const Tables& t, CollisionWork& cw, const double* w, d
     case 64: return collide_batch_n<64, double>(t, cw, w, c, ncells, s, launches, tm);
     case 128: return collide_batch_n<128, double>(t, cw, w, c, ncells, s, launches, tm);
     case 256: return collide_batch_n<256, double>(t, cw, w, c, ncells, s, launches, tm);
+    case 96: return collide_batch_n<96, double>(t, cw, w, c, ncells, s, launches, tm);
+    case 192: return collide_batch_n<192, double>(t, cw, w, c, ncells, s, launches, tm);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -40,6 +44,8 @@ cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int
       case 64: bps = i3_blocks_per_sm<64, float>(); break;
       case 128: bps = i3_blocks_per_sm<128, float>(); break;
       case 256: bps = i3_blocks_per_sm<256, float>(); break;
+      case 96: bps = i3_blocks_per_sm<96, float>(); break;
+      case 192: bps = i3_blocks_per_sm<192, float>(); break;
       default: return cudaErrorInvalidValue;
     }
   } else {
@@ -49,6 +55,8 @@ cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int
       case 64: bps = i3_blocks_per_sm<64, double>(); break;
       case 128: bps = i3_blocks_per_sm<128, double>(); break;
       case 256: bps = i3_blocks_per_sm<256, double>(); break;
+      case 96: bps = i3_blocks_per_sm<96, double>(); break;
+      case 192: bps = i3_blocks_per_sm<192, double>(); break;
       default: return cudaErrorInvalidValue;
     }
   }

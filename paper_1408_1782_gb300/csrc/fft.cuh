@@ -25,6 +25,8 @@ template <> struct Split<32>  { static constexpr int A = 4,  B = 8;  };
 template <> struct Split<64>  { static constexpr int A = 8,  B = 8;  };
 template <> struct Split<128> { static constexpr int A = 8,  B = 16; };
 template <> struct Split<256> { static constexpr int A = 16, B = 16; };
+template <> struct Split<96>  { static constexpr int A = 12, B = 8;  };
+template <> struct Split<192> { static constexpr int A = 12, B = 16; };
 
 // Frequency index (0..n-1, standard wrap) stored at permuted position pos.
 template <int n>
@@ -139,16 +141,76 @@ struct DftStage<R, SIGN, 2 * R, C2> {
   __device__ __forceinline__ static void run(C2 (&)[R]) {}
 };
 
-// In-register DFT of length R <= 16 (natural order in and out).
+// cos(2 pi k / 12) for integer k.
+__host__ __device__ constexpr double cos12(int k) {
+  constexpr double h3 = 0.86602540378443864676;   // sqrt(3)/2
+  k = ((k % 12) + 12) % 12;
+  return k == 0 ? 1.0 : k == 1 ? h3 : k == 2 ? 0.5 : k == 3 ? 0.0 : k == 4 ? -0.5 : k == 5 ? -h3
+       : k == 6 ? -1.0 : k == 7 ? -h3 : k == 8 ? -0.5 : k == 9 ? 0.0 : k == 10 ? 0.5 : h3;
+}
+__host__ __device__ constexpr double sin12(int k) { return cos12(k - 3); }
+
+// In-register DFT of length R (natural order in and out): R a power of two <= 16
+// (radix-2 decimation in time), or R = 3 * 2^q <= 12 (one radix-3 decimation-in-time
+// step on top of power-of-two sub-DFTs).
+template <int R, int SIGN, class C2, bool POW2 = ((R & (R - 1)) == 0)>
+struct Dft;
+
+template <int R, int SIGN, class C2>
+struct Dft<R, SIGN, C2, true> {
+  __device__ __forceinline__ static void run(C2 (&a)[R]) {
+    constexpr int L2 = ilog2c(R);
+    C2 b[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) b[i] = a[bitrev(i, L2)];
+    DftStage<R, SIGN, 2, C2>::run(b);
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = b[i];
+  }
+};
+
+template <int R, int SIGN, class C2>
+struct Dft<R, SIGN, C2, false> {
+  static_assert(R % 3 == 0 && R <= 12, "mixed-radix DFT supports 3, 6, 12");
+  __device__ __forceinline__ static void run(C2 (&a)[R]) {
+    using T = typename RealOf<C2>::type;
+    constexpr int Q = R / 3;
+    C2 s0[Q], s1[Q], s2[Q];
+#pragma unroll
+    for (int t = 0; t < Q; ++t) { s0[t] = a[3 * t]; s1[t] = a[3 * t + 1]; s2[t] = a[3 * t + 2]; }
+    Dft<Q, SIGN, C2>::run(s0);
+    Dft<Q, SIGN, C2>::run(s1);
+    Dft<Q, SIGN, C2>::run(s2);
+    const T h3 = (T)(SIGN * 0.86602540378443864676);   // SIGN * sqrt(3)/2
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      // twiddles exp(SIGN 2 pi i r k / R), r = 1, 2 (angles in twelfths: (12/R) r k)
+      const int e1 = (12 / R) * k, e2 = 2 * (12 / R) * k;
+      const C2 x0 = s0[k];
+      C2 x1 = s1[k], x2 = s2[k];
+      if (e1 % 12 != 0) {
+        const T c = (T)cos12(e1), sn = (T)(SIGN * sin12(e1));
+        x1 = mk2(fmaT(x1.x, c, -x1.y * sn), fmaT(x1.x, sn, x1.y * c));
+      }
+      if (e2 % 12 != 0) {
+        const T c = (T)cos12(e2), sn = (T)(SIGN * sin12(e2));
+        x2 = mk2(fmaT(x2.x, c, -x2.y * sn), fmaT(x2.x, sn, x2.y * c));
+      }
+      // radix-3 butterfly with w = exp(SIGN 2 pi i / 3)
+      const C2 t1 = cadd(x1, x2);
+      const C2 t2 = mk2(fmaT((T)-0.5, t1.x, x0.x), fmaT((T)-0.5, t1.y, x0.y));
+      const C2 d = csub(x1, x2);
+      const C2 t3 = mk2(-h3 * d.y, h3 * d.x);   // i * SIGN * sqrt(3)/2 * (x1 - x2)
+      a[k] = cadd(x0, t1);
+      a[k + Q] = cadd(t2, t3);
+      a[k + 2 * Q] = csub(t2, t3);
+    }
+  }
+};
+
 template <int R, int SIGN, class C2>
 __device__ __forceinline__ void dft(C2 (&a)[R]) {
-  constexpr int L2 = ilog2c(R);
-  C2 b[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) b[i] = a[bitrev(i, L2)];
-  DftStage<R, SIGN, 2, C2>::run(b);
-#pragma unroll
-  for (int i = 0; i < R; ++i) a[i] = b[i];
+  Dft<R, SIGN, C2>::run(a);
 }
 
 // FFT of nl lines of length n held in shared (or global) memory:
@@ -265,9 +327,13 @@ __device__ __forceinline__ void fft_conv_lines(C2* buf, int nl, int ls, int es, 
 // Chunk sizes (rows per row-pass chunk, columns per column-pass chunk) so that a
 // chunk of complex doubles occupies about 64 KB of shared memory (three blocks
 // per SM fit) and the radix-B stage has at least one task per thread.
+__host__ __device__ constexpr int largest_divisor_le(int n, int cap) {
+  return cap >= n ? n : (n % cap == 0 ? cap : largest_divisor_le(n, cap - 1));
+}
+
 template <int n, int ELEM = 16> struct Chunk {
   static constexpr int RC0 = 65536 / (n * ELEM);
-  static constexpr int RC = RC0 >= n ? n : RC0;
+  static constexpr int RC = largest_divisor_le(n, RC0);
   static constexpr int CC = RC;
   static constexpr int LS = n + 1;                 // padded row stride (odd => no bank conflicts)
   static constexpr int SMEM_ELEMS = (RC * LS > CC * n ? RC * LS : CC * n);

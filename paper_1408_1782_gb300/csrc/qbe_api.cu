@@ -97,6 +97,13 @@ int do_rk2(qbe_handle* h, double dt) {
   return QBE_OK;
 }
 
+int do_step(qbe_handle* h, double dt) {
+  int r = do_advect(h, 0.5 * dt);
+  if (!r) r = do_rk2(h, dt);
+  if (!r) r = do_advect(h, 0.5 * dt);
+  return r;
+}
+
 bool valid_fd(const qbe_fd* f) {
   return f && std::isfinite(f->beta) && f->beta > 0 && std::isfinite(f->mu_up) && std::isfinite(f->mu_dn);
 }
@@ -109,7 +116,7 @@ int qbe_create(const qbe_grid* g, qbe_handle** out) {
   if (!out) return QBE_ERR_ARG;
   *out = nullptr;
   if (!g) return QBE_ERR_ARG;
-  const bool n_ok = g->N == 8 || g->N == 16 || g->N == 32 || g->N == 64 || g->N == 128;
+  const bool n_ok = g->N == 8 || g->N == 16 || g->N == 32 || g->N == 48 || g->N == 64 || g->N == 96 || g->N == 128;
   if (!n_ok || g->Nx < 1 || g->J < 2 || g->J > 64 || (g->J % 2) != 0 || g->M < 1 || g->M > 64 ||
       !(g->L > 0) || !(g->R > 0) || !std::isfinite(g->L) || !std::isfinite(g->R))
     return QBE_ERR_ARG;
@@ -308,9 +315,7 @@ int qbe_step(qbe_handle* h, double dt, int nsteps) {
   if (!std::isfinite(dt) || nsteps < 0) return fail(h, QBE_ERR_ARG, "bad dt or nsteps");
   DeviceGuard dg(h->g.device);
   for (int s = 0; s < nsteps; ++s) {
-    int r = do_advect(h, 0.5 * dt);
-    if (!r) r = do_rk2(h, dt);
-    if (!r) r = do_advect(h, 0.5 * dt);
+    const int r = do_step(h, dt);
     if (r) return r;
   }
   return QBE_OK;
@@ -339,6 +344,209 @@ int qbe_moments(qbe_handle* h, double* rho, double* mom, double* energy, int on_
   if (e == cudaSuccess && mom) e = cudaMemcpy(mom, m2.data(), m2.size() * sizeof(double), k);
   if (e == cudaSuccess && energy) e = cudaMemcpy(energy, en.data(), en.size() * sizeof(double), k);
   return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "moments copy");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent simulations: one CUDA graph launch per split step.
+// ---------------------------------------------------------------------------
+
+struct qbe_batch {
+  std::vector<qbe_handle*> sims;
+  int device = 0;
+  cudaStream_t stream = nullptr;          // launch stream (caller's)
+  std::vector<cudaStream_t> side;         // one capture branch per simulation
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double graph_dt = 0.0;
+  std::vector<double> tuned_ms;
+  std::string err;
+};
+
+namespace {
+
+int bfail(qbe_batch* b, int code, const std::string& msg) {
+  b->err = msg;
+  return code;
+}
+
+void drop_graph(qbe_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qbe_batch_create(qbe_handle* const* sims, int nsims, qbe_batch** out) {
+  if (!out) return QBE_ERR_ARG;
+  *out = nullptr;
+  if (!sims || nsims < 1) return QBE_ERR_ARG;
+  for (int i = 0; i < nsims; ++i)
+    if (!sims[i] || sims[i]->g.device != sims[0]->g.device) return QBE_ERR_ARG;
+  for (int i = 0; i < nsims; ++i)
+    for (int k = 0; k < i; ++k)
+      if (sims[i] == sims[k]) return QBE_ERR_ARG;                  // each simulation once
+  qbe_batch* b = new (std::nothrow) qbe_batch();
+  if (!b) return QBE_ERR_ALLOC;
+  b->sims.assign(sims, sims + nsims);
+  b->device = sims[0]->g.device;
+  b->tuned_ms.assign(nsims, 0.0);
+  DeviceGuard dg(b->device);
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < nsims; ++i) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    b->side.push_back(st);
+    b->join.push_back(ev);
+  }
+  if (!ok) {
+    qbe_batch_destroy(b);
+    return QBE_ERR_CUDA;
+  }
+  *out = b;
+  return QBE_OK;
+}
+
+void qbe_batch_destroy(qbe_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->device);
+  drop_graph(b);
+  for (auto st : b->side) if (st) cudaStreamDestroy(st);
+  for (auto ev : b->join) if (ev) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+const char* qbe_batch_last_error(const qbe_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int qbe_batch_set_stream(qbe_batch* b, void* stream) {
+  if (!b) return QBE_ERR_ARG;
+  b->stream = (cudaStream_t)stream;
+  return QBE_OK;
+}
+
+int qbe_batch_autotune(qbe_batch* b) {
+  if (!b) return QBE_ERR_ARG;
+  DeviceGuard dg(b->device);
+  drop_graph(b);                                       // launch shapes are baked into the graph
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return bfail(b, QBE_ERR_CUDA, "autotune: event creation failed");
+  int rc = QBE_OK;
+  for (size_t i = 0; i < b->sims.size() && rc == QBE_OK; ++i) {
+    qbe_handle* h = b->sims[i];
+    if (!h->has_state) { rc = bfail(b, QBE_ERR_STATE, "autotune: a simulation has no state"); break; }
+    CollisionWork& cw = h->cw;
+    const int grid_max = cw.grid_i3, nmc_max = cw.nmc;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    const bool was_on = h->timer.on;
+    h->timer.on = false;
+    double best = 1e300;
+    int best_grid = grid_max, best_nmc = nmc_max;
+    // candidates: persistent I3 grid of 1..3 blocks per SM, m-chunk counts nmc_max, nmc_max/2, .., 1
+    for (int bps = 1; bps * nsm <= grid_max; ++bps) {
+      for (int nmc = nmc_max; nmc >= 1; nmc = (nmc == 1 ? 0 : (nmc + 1) / 2)) {
+        cw.grid_i3 = bps * nsm;
+        cw.mch = (h->g.M + nmc - 1) / nmc;
+        cw.nmc = (h->g.M + cw.mch - 1) / cw.mch;
+        int r = do_collide_dev(h, h->W, h->Cb, h->g.Nx);                    // warm
+        cudaEventRecord(e0, h->stream);
+        if (!r) r = do_collide_dev(h, h->W, h->Cb, h->g.Nx);
+        cudaEventRecord(e1, h->stream);
+        float ms = 0.f;
+        if (!r && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+          if (ms < best) { best = ms; best_grid = cw.grid_i3; best_nmc = cw.nmc; }
+        } else {
+          rc = bfail(b, QBE_ERR_CUDA, "autotune: timing run failed");
+          break;
+        }
+        if (nmc == 1) break;
+      }
+      if (rc) break;
+    }
+    cw.grid_i3 = best_grid;
+    cw.mch = (h->g.M + best_nmc - 1) / best_nmc;
+    cw.nmc = (h->g.M + cw.mch - 1) / cw.mch;
+    h->timer.on = was_on;
+    b->tuned_ms[i] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int qbe_batch_tuned_shape(const qbe_batch* b, int sim, int* i3_grid, int* m_chunks, double* ms) {
+  if (!b || sim < 0 || sim >= (int)b->sims.size()) return QBE_ERR_ARG;
+  if (i3_grid) *i3_grid = b->sims[sim]->cw.grid_i3;
+  if (m_chunks) *m_chunks = b->sims[sim]->cw.nmc;
+  if (ms) *ms = b->tuned_ms[sim];
+  return QBE_OK;
+}
+
+int qbe_batch_step(qbe_batch* b, double dt, int nsteps) {
+  if (!b) return QBE_ERR_ARG;
+  if (!std::isfinite(dt) || nsteps < 0) return bfail(b, QBE_ERR_ARG, "bad dt or nsteps");
+  for (auto h : b->sims)
+    if (!h->has_state) return bfail(b, QBE_ERR_STATE, "a simulation has no state");
+  DeviceGuard dg(b->device);
+  if (!b->exec || b->graph_dt != dt) {
+    drop_graph(b);
+    cudaError_t e = cudaStreamBeginCapture(b->stream ? b->stream : b->side[0], cudaStreamCaptureModeThreadLocal);
+    // the legacy default stream cannot be captured: capture on the first branch stream instead
+    cudaStream_t origin = b->stream ? b->stream : b->side[0];
+    if (e != cudaSuccess) return bfail(b, QBE_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    int r = QBE_OK;
+    cudaEventRecord(b->fork, origin);
+    for (size_t i = 0; i < b->sims.size() && r == QBE_OK; ++i) {
+      qbe_handle* h = b->sims[i];
+      cudaStream_t br = (origin == b->side[i]) ? origin : b->side[i];
+      if (br != origin) cudaStreamWaitEvent(br, b->fork, 0);
+      const cudaStream_t saved = h->stream;
+      const bool was_on = h->timer.on;
+      h->timer.on = false;
+      h->stream = br;
+      r = do_step(h, dt);                     // even number of state-buffer swaps: ends in h->W again
+      h->stream = saved;
+      h->timer.on = was_on;
+      if (br != origin) {
+        cudaEventRecord(b->join[i], br);
+        cudaStreamWaitEvent(origin, b->join[i], 0);
+      }
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(origin, &g);
+    if (r != QBE_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(b, r != QBE_OK ? r : QBE_ERR_CUDA, "capture of the batched step failed");
+    }
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+      drop_graph(b);
+      return bfail(b, QBE_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    b->graph_dt = dt;
+  }
+  cudaStream_t launch = b->stream ? b->stream : b->side[0];
+  for (int s = 0; s < nsteps; ++s) {
+    cudaError_t e = cudaGraphLaunch(b->exec, launch);
+    if (e != cudaSuccess) return bfail(b, QBE_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  }
+  if (!b->stream) {
+    cudaError_t e = cudaStreamSynchronize(launch);
+    if (e != cudaSuccess) return bfail(b, QBE_ERR_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
+  }
+  return QBE_OK;
 }
 
 }  // extern "C"

@@ -19,6 +19,8 @@ void split_of(int n, int& A, int& B) {
     case 64: A = 8; B = 8; break;
     case 128: A = 8; B = 16; break;
     case 256: A = 16; B = 16; break;
+    case 96: A = 12; B = 8; break;
+    case 192: A = 12; B = 16; break;
     default: A = B = 0;
   }
 }
@@ -108,7 +110,7 @@ bool build_tables(int N, int J, int M, double L, double R, Tables& t, std::strin
   int A = 0, B = 0;
   split_of(n, A, B);
   if (A == 0) {
-    err = "unsupported N (supported: 8, 16, 32, 64, 128)";
+    err = "unsupported N (supported: 8, 16, 32, 48, 64, 96, 128)";
     return false;
   }
   t.N = N; t.n = n; t.J = J; t.M = M; t.L = L; t.R = R;

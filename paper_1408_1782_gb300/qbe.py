@@ -52,6 +52,14 @@ SIGNATURES = {
     "qbe_enable_timing": (_c_int, [_c_void_p, _c_int]),
     "qbe_kernel_time": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "qbe_collide_noalloc": (_c_int, [ctypes.POINTER(QbeGrid), _c_void_p, _c_void_p, _c_int, _c_void_p]),
+    "qbe_batch_create": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, ctypes.POINTER(_c_void_p)]),
+    "qbe_batch_destroy": (None, [_c_void_p]),
+    "qbe_batch_last_error": (ctypes.c_char_p, [_c_void_p]),
+    "qbe_batch_set_stream": (_c_int, [_c_void_p, _c_void_p]),
+    "qbe_batch_autotune": (_c_int, [_c_void_p]),
+    "qbe_batch_tuned_shape": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                       ctypes.POINTER(_c_double)]),
+    "qbe_batch_step": (_c_int, [_c_void_p, _c_double, _c_int]),
 }
 
 KERNEL_GROUPS = {"prep": 0, "i1": 1, "i24": 2, "i3": 3, "assemble": 4, "transport": 5, "rk": 6}
@@ -105,6 +113,51 @@ def _arg(x, shape):
             raise ValueError(f"expected contiguous float64 tensor of shape {tuple(shape)}")
         return x.data_ptr(), 1 if x.is_cuda else 0, x
     raise TypeError(f"unsupported array type {type(x)}")
+
+
+class Batch:
+    """Independent simulations stepped together, one CUDA graph launch per split step."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        arr = (_c_void_p * len(self.solvers))(*[s._h for s in self.solvers])
+        h = _c_void_p()
+        rc = lib().qbe_batch_create(arr, len(self.solvers), ctypes.byref(h))
+        if rc != 0:
+            raise QbeError(f"qbe_batch_create failed with code {rc}")
+        self._b = h
+        if stream is not None:
+            handle = getattr(stream, "cuda_stream", stream)
+            self._check(lib().qbe_batch_set_stream(self._b, _c_void_p(int(handle) if handle else 0)), "set_stream")
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = lib().qbe_batch_last_error(self._b)
+            raise QbeError(f"{what} failed ({rc}): {msg.decode() if msg else ''}")
+
+    def autotune(self):
+        self._check(lib().qbe_batch_autotune(self._b), "qbe_batch_autotune")
+        out = []
+        for i in range(len(self.solvers)):
+            g, m, ms = _c_int(), _c_int(), _c_double()
+            self._check(lib().qbe_batch_tuned_shape(self._b, i, ctypes.byref(g), ctypes.byref(m), ctypes.byref(ms)),
+                        "qbe_batch_tuned_shape")
+            out.append((g.value, m.value, ms.value))
+        return out
+
+    def step(self, dt, nsteps=1):
+        self._check(lib().qbe_batch_step(self._b, float(dt), int(nsteps)), "qbe_batch_step")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().qbe_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def collide_noalloc(w, out, J=32, M=32, L=12.0, R=7.5, stream=None):

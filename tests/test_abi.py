@@ -62,11 +62,11 @@ def test_create_rejects_bad_arguments_without_touching_a_gpu(libpath):
 
     L = qbe.lib()
     h = ctypes.c_void_p()
-    for bad in (dict(N=12), dict(N=16, J=5), dict(N=16, M=0), dict(N=16, Nx=0), dict(N=16, L=-1.0)):
+    for bad in (dict(N=12), dict(N=40), dict(N=16, J=5), dict(N=16, M=0), dict(N=16, Nx=0), dict(N=16, L=-1.0)):
         args = dict(N=16, Nx=4, J=8, M=8, L=12.0, R=7.5)
         args.update(bad)
         g = qbe.QbeGrid(args["N"], args["Nx"], args["J"], args["M"], args["L"], args["R"], 0, 0)
         assert L.qbe_create(ctypes.byref(g), ctypes.byref(h)) == -1
-    g = qbe.QbeGrid(16, 4, 8, 8, 12.0, 7.5, 1, 0)
+    g = qbe.QbeGrid(16, 4, 8, 8, 12.0, 7.5, 2, 0)
     assert L.qbe_create(ctypes.byref(g), ctypes.byref(h)) == -5
     assert L.qbe_create(None, ctypes.byref(h)) == -1
