@@ -210,4 +210,13 @@ WORKLOADS = {
     "precision_n128": dict(N=128, Nx=256, L=12.0, R=7.5, J=32, M=32, bc="maxwell", alpha=0.5,
                            wall=dict(beta=1.0, mu_up=0.0, mu_dn=0.0),
                            B=(0.3, 0.0, 0.4), dt=0.002, steps=200, perturb=0.05, precision=1),
+    # gradient of the final-time spin polarisation and energy flux w.r.t. the initial W and B
+    "adjoint_n64": dict(N=64, Nx=128, L=12.0, R=7.5, J=32, M=32, bc="periodic",
+                        B=(0.3, 0.0, 0.4), dt=0.005, steps=200, checkpoint_every=20, perturb=0.05, precision=1),
 }
+
+
+def random_field(shape, seed: int = 0, scale: float = 1.0) -> np.ndarray:
+    """Seeded standard-normal field of the given shape (tangent directions and cotangents)."""
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(scale * rng.standard_normal(shape))

@@ -16,7 +16,13 @@ applied to the seeded synthetic inputs; nothing comes from the CUDA library.
                        Maxwell workload's initial state (5% perturbation) and
                        their C[W] (the FP32-split form is checked against it).
 
-Usage: python tests/golden/make_golden.py [n16|n64|n128|all]
+  collision_vjp_n8.npz
+                       N=8, J=4, M=2: two cells (5% perturbation), a seeded
+                       cotangent lam and the transposed derivative
+                       (dC/dW)^T lam assembled column by column from exact
+                       directional derivatives of the oracle (oracle/tangent.py).
+
+Usage: python tests/golden/make_golden.py [n16|n64|n128|vjp8|all]
 """
 import os
 import sys
@@ -29,6 +35,7 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 from oracle import qbe_oracle as O  # noqa: E402
+from oracle import tangent as T  # noqa: E402
 from paper_1408_1782_gb300 import inputs  # noqa: E402
 
 
@@ -78,6 +85,19 @@ def make_n128():
     np.savez_compressed(os.path.join(HERE, "precision_n128_cells.npz"), cells=cells, W=W[cells], C=C)
 
 
+def make_vjp8():
+    import multiprocessing as mp
+
+    p = O.Params(N=8, J=4, M=2)
+    W = inputs.synthetic_w(8, 2, seed=31, perturb=0.05)
+    lam = inputs.random_field(W.shape, seed=32)
+    t = time.time()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        G = T.collision_vjp_brute(W, lam, p, mapper=lambda f, it: pool.map(f, list(it), chunksize=4))
+    print(f"vjp8 {time.time() - t:.1f}s", flush=True)
+    np.savez_compressed(os.path.join(HERE, "collision_vjp_n8.npz"), W=W, lam=lam, grad=G, N=8, J=4, M=2)
+
+
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "all"
     if which in ("n64", "all"):
@@ -86,3 +106,5 @@ if __name__ == "__main__":
         make_n16()
     if which in ("n128", "all"):
         make_n128()
+    if which in ("vjp8", "all"):
+        make_vjp8()
