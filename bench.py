@@ -222,6 +222,8 @@ def run_ours(args):
 
     if args.workload == "batched_16":
         return run_batched(args, local)
+    if args.workload == "adjoint_n64":
+        return run_adjoint(args, local)
     wl = workload(args.workload, args.precision)
     if args.mode == "collide":
         return run_collide_only(args, wl, local)
@@ -483,6 +485,172 @@ def run_collide_only(args, wl, local):
     return 0
 
 
+def i3_vjp_flops_per_unit(N):
+    """Algorithmic FLOPs of one (cell, j, m) unit of the I3 transpose kernel, same convention as
+    i3_flops_per_unit: 72 real 2-D transforms (4 for the two shifts, 64 for the 16 convolutions of
+    complex pairs, 4 for the two forward transforms of the shifted-back sums) at 2.5 P log2 P each,
+    plus 228 P pointwise flops (shift phases, 16 scalings, 16 psi' products, the three pointwise
+    sums per component, the conjugate phases and spectral accumulation)."""
+    P = (2 * N) ** 2
+    return 180.0 * P * math.log2(P) + 228.0 * P
+
+
+def run_adjoint(args, local):
+    """Gradient of the final-time spin polarisation P_z and energy flux Phi_E with respect to the
+    initial state W_0 and the field B: forward sweep (qbe_step_checkpointed over the horizon) and
+    reverse sweep (qbe_observables_vjp + qbe_step_vjp).  One timed step = one gradient of both
+    observables (one forward sweep, two reverse sweeps)."""
+    import numpy as np
+    import torch
+
+    from paper_1408_1782_gb300 import inputs, qbe
+
+    wl = workload("adjoint_n64", args.precision)
+    N, Nx, prec = wl["N"], wl["Nx"], wl.get("precision", 0)
+    H = args.horizon or wl["checkpoint_every"]
+    every = min(wl["checkpoint_every"], H)
+    stream = torch.cuda.current_stream()
+    s = qbe.Solver(N, Nx, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream,
+                   precision=prec)
+    B = torch.from_numpy(inputs.uniform_b(Nx, wl["B"])).cuda()
+    W0 = torch.from_numpy(inputs.synthetic_w(N, Nx, L=wl["L"], seed=0, perturb=wl["perturb"])).cuda()
+    lam = torch.empty_like(W0)
+    lam0 = torch.empty_like(W0)
+    gB = torch.empty_like(B)
+    obs = torch.empty(2, dtype=torch.float64, device="cuda")
+    seeds = [torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda"),
+             torch.tensor([0.0, 1.0], dtype=torch.float64, device="cuda")]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def gradient(events=None):
+        s.set_state(W0)
+        s.set_bfield(B)
+        if events:
+            events[0].record(stream)
+        s.step_checkpointed(wl["dt"], H, every)
+        s.observables(None, out=obs)
+        if events:
+            events[1].record(stream)
+        for g in seeds:
+            s.observables_vjp(g, out=lam)
+            s.step_vjp(lam, out=lam0, grad_B=gB)
+        if events:
+            events[2].record(stream)
+
+    for _ in range(args.warmup):
+        gradient()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    s.enable_timing(True)
+    launches0 = s.launch_count()
+    clocks.start()
+    fwd, rev = 0.0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e = [ev(), ev(), ev()]
+        gradient(e)
+        torch.cuda.synchronize()
+        fwd += e[0].elapsed_time(e[1])
+        rev += e[1].elapsed_time(e[2])
+    clk = clocks.stop()
+    launches = s.launch_count() - launches0
+    vi3_ms, vi3_n = s.kernel_time("vjp_i3")
+    groups = {gname: s.kernel_time(gname)[0] for gname in qbe.KERNEL_GROUPS}
+    s.enable_timing(False)
+    # per reverse sweep (one observable): ratio to the forward sweep it differentiates
+    ratio = (rev / 2.0) / fwd
+    avg_vi3 = vi3_ms * 1e-3 / max(vi3_n, 1)
+    flops = Nx * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N)
+    sm_max = 2070.0
+    try:
+        sm_max = float(json.load(open(MEASURED_PEAKS)).get("sm_max_mhz", sm_max))
+    except Exception:
+        pass
+    lanes = FP64_FMA_PER_CLK_PER_SM if prec == 0 else FP32_FMA_PER_CLK_PER_SM
+    peak = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / avg_vi3 / 1e12
+
+    # end to end through host buffers: state and field in from pinned host memory, gradients out
+    hW = W0.cpu().pin_memory()
+    hB = B.cpu().pin_memory()
+    hl = torch.empty_like(hW).pin_memory()
+    hl0 = torch.empty_like(hW).pin_memory()
+    hgB = torch.empty_like(hB).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(hW)
+    s.set_bfield(hB)
+    s.step_checkpointed(wl["dt"], H, every)
+    obs_host = s.observables()            # D2H of the observables (synchronises)
+    t1 = time.perf_counter()
+    s.observables_vjp(np.array([1.0, 0.0]), out=hl)
+    s.step_vjp(hl, out=hl0, grad_B=hgB)
+    t2 = time.perf_counter()
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = adjoint_cpu_baseline(wl)
+    conf = config_dict(dict(wl, name="adjoint_n64"), 1)
+    conf.update({"horizon_steps": H, "checkpoint_every": every,
+                 "workload": conf["workload"] + f"; gradient of P_z and Phi_E after {H} split steps "
+                                                f"(checkpoint every {every}) w.r.t. W_0 and B"})
+    line = {
+        "metric": "adjoint/forward time ratio", "value": ratio, "unit": "reverse sweep s / forward sweep s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (fwd + rev) / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32-split",
+        "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)", "config": conf,
+        "forward_ms_per_split_step": fwd / args.steps / H,
+        "reverse_ms_per_split_step": rev / args.steps / H / 2.0,
+        "gradients_per_s": 2e3 * args.steps / (fwd + rev),
+        "observables": obs.cpu().tolist(),
+        "roofline": {"kernel": "k_i3_vjp (transpose of the Hu-Ying I3 term)", "bound": "alu",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "flops_per_launch": flops, "avg_launch_ms": avg_vi3 * 1e3,
+                     "peak_source": (f"derived: {SM_COUNT} SMs x {lanes} {'FP64' if prec == 0 else 'FP32'} "
+                                     f"FMA/clk x 2 flop x {sm_max:.0f} MHz")},
+        "kernel_ms": {k: round(v, 2) for k, v in groups.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": (t2 - t1) / (t1 - t0), "unit": "reverse sweep s / forward sweep s",
+                "h2d_bytes_per_step": hW.numel() * 8 + hB.numel() * 8 + 16,
+                "d2h_bytes_per_step": obs_host.nbytes + hl.numel() * 8 * 2 + hgB.numel() * 8,
+                "note": "one observable's gradient; forward sweep incl. H2D of W_0 and B, reverse incl. D2H"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
+def adjoint_cpu_baseline(wl):
+    """The oracle's derivative of C[W] along one direction for one cell (forward mode: four C[W]
+    evaluations of the five-point difference), on up to 16 spawned processes."""
+    import multiprocessing as mp
+
+    from oracle import qbe_oracle as O
+    from oracle import tangent as T
+    from paper_1408_1782_gb300 import inputs
+
+    p = O.Params(N=wl["N"], L=wl["L"], R=wl["R"], J=wl["J"], M=wl["M"])
+    W = inputs.synthetic_w(wl["N"], 1, L=wl["L"], seed=0, perturb=wl["perturb"])
+    dW = inputs.random_field(W.shape, seed=1, scale=0.05)
+    ncores = min(16, host_cores())
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        t = time.perf_counter()
+        T.collision_jvp(W, dW, p, mapper=lambda f, it: pool.map(f, list(it), chunksize=1))
+        dt = time.perf_counter() - t
+    return {"value": wl["N"] ** 2 / dt, "unit": "cell·k-pts/s of dC/dW products", "cores": ncores,
+            "kind": "oracle",
+            "sample": f"one directional derivative of C[W] for 1 cell (N={wl['N']}, J=M={wl['J']}), {dt:.1f} s"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -492,8 +660,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["step", "collide"], default="step")
-    ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128", "batched_16"],
+    ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128", "batched_16", "adjoint_n64"],
                     default="plain_fp64_n64")
+    ap.add_argument("--horizon", type=int, default=0,
+                    help="adjoint_n64: split steps per gradient (default: one checkpoint segment, 20)")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None)
     ap.add_argument("--cells", type=int, default=0)
     args = ap.parse_args()

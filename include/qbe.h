@@ -144,6 +144,53 @@ int qbe_step(qbe_handle* h, double dt, int nsteps);
  * sums times (2L/N)^2.  Any output pointer may be NULL. */
 int qbe_moments(qbe_handle* h, double* rho, double* mom, double* energy, int on_device);
 
+/* ---- Differentiation -------------------------------------------------
+ * The paper computes no derivatives: these entry points are exact
+ * vector-Jacobian products (transposed derivatives) of the discrete maps
+ * above, for gradients of a final-time observable with respect to the
+ * initial state and the field B.  C[W] is a cubic polynomial in W (eq.
+ * CcPauli, eq. CdPauli), so its derivative is the same family of FFT
+ * convolutions with reflected multipliers; the transport update (eq.
+ * slopeLimiterStep) is differentiated at the minmod branches (eq. minmod) the
+ * forward call takes (a tie |a| = |b| takes a's branch), the Maxwell wall's
+ * outgoing flux (Sec. 2) as the linear functional it is, and the precession
+ * term -i[B.sigma, W] = 2 (B x w).sigma as the bilinear map it is.  Each
+ * product is computed in the handle's precision form. */
+
+/* grad = (dC/dW at w)^T lam for ncells independent cells: w, lam, grad
+ * [ncells][4][N][N] (grad may alias lam).  Does not touch the solver state.
+ * The first call allocates the product's workspace (about twice the
+ * collision workspace).  Errors: QBE_ERR_ARG, QBE_ERR_ALLOC, QBE_ERR_CUDA. */
+int qbe_collide_vjp(qbe_handle* h, const double* w, const double* lam, double* grad, int ncells, int on_device);
+
+/* qbe_step(h, dt, nsteps) that also records a tape for qbe_step_vjp: the
+ * state before every checkpoint_every-th step (ceil(nsteps/checkpoint_every)
+ * states of device memory, kept by h and reused).  Any later call that
+ * changes the state, the field or the boundary invalidates the tape.
+ * Errors: QBE_ERR_ARG (nsteps < 1, checkpoint_every < 1), QBE_ERR_STATE. */
+int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_every);
+
+/* Reverse sweep over the tape of the last qbe_step_checkpointed(h, dt,
+ * nsteps, k) call, which mapped W_0 to W_n: lam_init = (dW_n/dW_0)^T
+ * lam_final ([Nx][4][N][N]) and, if grad_B is not NULL, grad_B =
+ * (dW_n/dB)^T lam_final ([Nx][3]).  Each segment of k steps is recomputed from
+ * its checkpoint with every intermediate state kept (k (2 s + 2) states, s
+ * the transport substeps of a half step), then swept backwards.  The state
+ * is W_n again on return.  Errors: QBE_ERR_STATE (no valid tape),
+ * QBE_ERR_ARG, QBE_ERR_ALLOC, QBE_ERR_CUDA. */
+int qbe_step_vjp(qbe_handle* h, const double* lam_final, double* lam_init, double* grad_B, int on_device);
+
+/* Final-time observables of a state w[Nx][4][N][N] (NULL: the solver
+ * state): out[0] = P_z = dx dv^2 sum 2 w3 (total spin polarisation along z,
+ * tr(sigma_3 W) = 2 w3), out[1] = Phi_E = dx dv^2 sum v_x |v|^2/2 2 w0
+ * (energy flux, tr W = 2 w0), sums over all cells and velocities, dx = 1/Nx,
+ * dv = 2L/N (eqs. density, internal_energy).  w and out are both host or
+ * both device memory. */
+int qbe_observables(qbe_handle* h, const double* w, double* out, int on_device);
+
+/* lam = gbar[0] dP_z/dW + gbar[1] dPhi_E/dW ([Nx][4][N][N]); gbar[2]. */
+int qbe_observables_vjp(qbe_handle* h, const double* gbar, double* lam, int on_device);
+
 /* Number of kernel launches issued by the library since create (for
  * benchmarking bookkeeping). */
 long long qbe_launch_count(const qbe_handle* h);
@@ -162,6 +209,9 @@ long long qbe_launch_count(const qbe_handle* h);
 #define QBE_KG_ASSEMBLE 4
 #define QBE_KG_TRANSPORT 5
 #define QBE_KG_RK 6
+#define QBE_KG_VJP 7           /* collision product: recomputed forward terms, seed, I1/I2/I4 transposes, final */
+#define QBE_KG_VJP_I3 8        /* collision product: transpose of the I3 (Hu-Ying) term */
+#define QBE_KG_ADJ_TRANSPORT 9 /* transposes of the transport substeps and of the RK2 + precession update */
 int qbe_enable_timing(qbe_handle* h, int enable);
 int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launches);
 

@@ -99,4 +99,87 @@ void free_collision_work(CollisionWork& cw) {
   cw = CollisionWork();
 }
 
+
+#define QBE_VJP_SWITCH(T, CALL)                       \
+  switch (t.n) {                                      \
+    case 16: return CALL(16, T);                      \
+    case 32: return CALL(32, T);                      \
+    case 64: return CALL(64, T);                      \
+    case 128: return CALL(128, T);                    \
+    case 256: return CALL(256, T);                    \
+    case 96: return CALL(96, T);                      \
+    case 192: return CALL(192, T);                    \
+    default: break;                                   \
+  }
+
+namespace {
+int vjp_bps(const Tables& t, int prec) {
+#define QBE_BPS(n, T) i3_vjp_blocks_per_sm<n, T>()
+  if (prec == 1) {
+    QBE_VJP_SWITCH(float, QBE_BPS)
+  } else {
+    QBE_VJP_SWITCH(double, QBE_BPS)
+  }
+#undef QBE_BPS
+  return 0;
+}
+}  // namespace
+
+cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
+                        double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,
+                        KernelTimer* tm) {
+  if (ncells > cw.nb || ncells > vw.nb || cw.prec != vw.prec) return cudaErrorInvalidValue;
+#define QBE_VJP_CALL(n, T) collide_vjp_n<n, T>(t, cw, vw, w, lam, grad, ncells, accumulate, s, launches, tm)
+  if (vw.prec == 1) {
+    QBE_VJP_SWITCH(float, QBE_VJP_CALL)
+  } else {
+    QBE_VJP_SWITCH(double, QBE_VJP_CALL)
+  }
+#undef QBE_VJP_CALL
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec) {
+  const size_t P = (size_t)t.n * t.n;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int bps = vjp_bps(t, prec);
+  if (bps < 1) return cudaErrorInvalidValue;
+  vw.prec = prec;
+  vw.nb = nb;
+  vw.grid = nsm * bps;
+  // about 4 waves of (cell, j, m-chunk) units
+  int nmc = (4 * vw.grid + nb * t.J - 1) / (nb * t.J);
+  if (nmc < 1) nmc = 1;
+  if (nmc > t.M) nmc = t.M;
+  vw.mch = (t.M + nmc - 1) / nmc;
+  vw.nmc = (t.M + vw.mch - 1) / vw.mch;
+  const size_t nparts = (size_t)nb * t.J * vw.nmc;
+  size_t ws_fields = 7 * (size_t)nb;
+  if (9 * (size_t)vw.grid > ws_fields) ws_fields = 9 * (size_t)vw.grid;
+  const size_t cz = prec == 1 ? sizeof(float2) : sizeof(double2);
+  const size_t rz = cz / 2;
+  cudaError_t e;
+#define QBE_ALLOC(ptr, bytes) \
+  if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) { free_vjp_work(vw); return e; }
+  QBE_ALLOC(vw.nu, (size_t)nb * 2 * P * cz);
+  QBE_ALLOC(vw.nuf, (size_t)nb * P * rz);
+  QBE_ALLOC(vw.muD, (size_t)nb * 2 * P * cz);
+  QBE_ALLOC(vw.muK2, (size_t)nb * P * rz);
+  QBE_ALLOC(vw.mu4, (size_t)nb * 2 * P * cz);
+  QBE_ALLOC(vw.mu3, (size_t)nb * 2 * P * cz);
+  QBE_ALLOC(vw.part_r, nparts * 2 * P * cz);
+  QBE_ALLOC(vw.part_s, nparts * 2 * P * cz);
+  QBE_ALLOC(vw.ws, ws_fields * P * cz);
+#undef QBE_ALLOC
+  return cudaSuccess;
+}
+
+void free_vjp_work(VjpWork& vw) {
+  cudaFree(vw.nu); cudaFree(vw.nuf); cudaFree(vw.muD); cudaFree(vw.muK2); cudaFree(vw.mu4); cudaFree(vw.mu3);
+  cudaFree(vw.part_r); cudaFree(vw.part_s); cudaFree(vw.ws);
+  vw = VjpWork();
+}
+
 }  // namespace qbe

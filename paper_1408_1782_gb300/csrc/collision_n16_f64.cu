@@ -1,8 +1,11 @@
 // Instantiation of the collision kernels for the 16 x 16 padded grid (N = 8), FP64 transforms.
-#include "collision_kernels.cuh"
+#include "collision_vjp.cuh"
 
 namespace qbe {
 template cudaError_t collide_batch_n<16, double>(const Tables&, CollisionWork&, const double*, double*, int,
                                               cudaStream_t, long long&, KernelTimer*);
 template int i3_blocks_per_sm<16, double>();
+template cudaError_t collide_vjp_n<16, double>(const Tables&, CollisionWork&, VjpWork&, const double*, const double*,
+                                            double*, int, int, cudaStream_t, long long&, KernelTimer*);
+template int i3_vjp_blocks_per_sm<16, double>();
 }  // namespace qbe

@@ -1,8 +1,11 @@
 // Instantiation of the collision kernels for the 32 x 32 padded grid (N = 16), FP32 transforms.
-#include "collision_kernels.cuh"
+#include "collision_vjp.cuh"
 
 namespace qbe {
 template cudaError_t collide_batch_n<32, float>(const Tables&, CollisionWork&, const double*, double*, int,
                                               cudaStream_t, long long&, KernelTimer*);
 template int i3_blocks_per_sm<32, float>();
+template cudaError_t collide_vjp_n<32, float>(const Tables&, CollisionWork&, VjpWork&, const double*, const double*,
+                                            double*, int, int, cudaStream_t, long long&, KernelTimer*);
+template int i3_vjp_blocks_per_sm<32, float>();
 }  // namespace qbe

@@ -1,8 +1,11 @@
 // Instantiation of the collision kernels for the 64 x 64 padded grid (N = 32), FP32 transforms.
-#include "collision_kernels.cuh"
+#include "collision_vjp.cuh"
 
 namespace qbe {
 template cudaError_t collide_batch_n<64, float>(const Tables&, CollisionWork&, const double*, double*, int,
                                               cudaStream_t, long long&, KernelTimer*);
 template int i3_blocks_per_sm<64, float>();
+template cudaError_t collide_vjp_n<64, float>(const Tables&, CollisionWork&, VjpWork&, const double*, const double*,
+                                            double*, int, int, cudaStream_t, long long&, KernelTimer*);
+template int i3_vjp_blocks_per_sm<64, float>();
 }  // namespace qbe

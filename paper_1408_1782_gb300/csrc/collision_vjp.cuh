@@ -1,0 +1,618 @@
+// Vector-Jacobian product of the discrete collision operator: given a
+// cotangent lambda of C[W] on the velocity grid, the gradient of <lambda, C[W]>
+// with respect to W.  Used by the adjoint of the split time step.
+//
+// Every dependence of C on W goes through the fine-grid interpolant w^fine
+// = I(W) (band-limited to Xi), so the kernels accumulate a fine-grid cotangent
+// nu_a of each Pauli component and finish with I^T nu = 4 E P nu (band-limit
+// to Xi, sample the coarse nodes; E samples the even fine nodes).  The
+// transposes used, all exact for the discrete operators:
+//   * a Fourier multiplier m(sigma) transposes to m(-sigma): even real
+//     multipliers (psi, psi') are self-adjoint; odd ones are handled as the
+//     real operators "multiply by i phi'" and "multiply by i K", which are
+//     antisymmetric;
+//   * the Hu-Ying shift S (multiplier e^{i alpha.sigma}) transposes to the
+//     shift back (conjugate phase);
+//   * the projection of C_fine to Xi is self-adjoint; sampling transposes to
+//     zero interleaving.
+// With lambda band-limited by that projection, the only frequency at which
+// these statements need care (the unpaired -N line of the padded grid) never
+// reaches Xi.  Terms (as in the forward kernels, raw accumulators):
+//   D_b = -K'(f A_{j'} w_b),   K2 = 2 (pi/J) sum eta_a F_{a,j} F_{a,j+J/2},
+//   K4raw_b = (pi/J) sum_j Psi_j(f F_{b,j+J/2}),
+//   K3raw_b = sum_{j,m,a} eta_a S(w_a) Psi'_j(w_a S(w_b)),   f = 2 w0 - 1.
+#pragma once
+
+#include "collision_kernels.cuh"
+
+namespace qbe {
+
+namespace {
+
+template <class C2>
+__device__ __forceinline__ C2 mul_i(C2 v, typename RealOf<C2>::type s) {   // v * (i s)
+  return mk2(-s * v.y, s * v.x);
+}
+
+// --------------------------------------------------------------------------
+// Seed: mu = P(E^T lambda) on the fine grid, the forward D and K4 fields, and
+// the transpose of the pointwise Pauli assembly.  One block per cell.
+// Outputs: nu[c][2] (direct cotangent of the w pairs), nuf[c] (cotangent of
+// f = 2 w0 - 1), muD[c][2] (pairs (D1,D2),(D3,-)), muK2[c], mu4[c][2] (raw K4
+// pairs), mu3[c][2] (raw K3 pairs).
+// --------------------------------------------------------------------------
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads) k_vjp_seed(
+    const double* __restrict__ lam, const typename Vec2Of<T>::type* wfine, const typename Vec2Of<T>::type* Dacc,
+    const T* K2acc, const typename Vec2Of<T>::type* K4acc, typename Vec2Of<T>::type* nu, T* nuf,
+    typename Vec2Of<T>::type* muD, T* muK2, typename Vec2Of<T>::type* mu4, typename Vec2Of<T>::type* mu3,
+    typename Vec2Of<T>::type* ws, const typename Vec2Of<T>::type* __restrict__ gtw) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
+  load_twiddles<n>(tw, gtw);
+  constexpr int N = n / 2, P = n * n;
+  const int c = blockIdx.x;
+  C2* slot = ws + (size_t)blockIdx.x * 6 * P;
+  C2* MU = slot;             // [2] cotangent of C_fine pairs (0,1), (2,3)
+  C2* DK = slot + 2 * P;     // [4] D pairs, K4 pairs in real space
+  const double* lc = lam + (size_t)c * 4 * N * N;
+  const T invP = (T)(1.0 / (double)P);
+  for (int p = 0; p < 2; ++p) {
+    C2* M = MU + (size_t)p * P;
+    row_pass<n, -1, false, 0>(
+        sm, tw,
+        [&](int ix, int iy) {
+          if ((ix | iy) & 1) return zero2<T>();
+          const int i = ix >> 1, j = iy >> 1;
+          return mk2((T)lc[((2 * p) * N + i) * N + j], (T)lc[((2 * p + 1) * N + i) * N + j]);
+        },
+        NoMid(), [&](int ix, int iy, C2 v) { M[ix * n + iy] = v; });
+    col_pass<n, -1, true, 1>(
+        sm, tw, [&](int ix, int iy) { return M[ix * n + iy]; },
+        [&](int ix, int iy, C2 v) {
+          const bool keep = in_xi<n>(freq_of_pos<n>(ix)) && in_xi<n>(freq_of_pos<n>(iy));
+          return keep ? cscale(v, invP) : zero2<T>();
+        },
+        [&](int ix, int iy, C2 v) { M[ix * n + iy] = v; });
+    row_pass<n, 1, false, 0>(
+        sm, tw, [&](int ix, int iy) { return M[ix * n + iy]; }, NoMid(),
+        [&](int ix, int iy, C2 v) { M[ix * n + iy] = v; });
+  }
+  for (int f = 0; f < 4; ++f) {
+    const C2* in = (f < 2) ? (Dacc + ((size_t)c * 2 + f) * P) : (K4acc + ((size_t)c * 2 + (f - 2)) * P);
+    C2* out = DK + (size_t)f * P;
+    col_pass<n, 1, false, 0>(
+        sm, tw, [&](int ix, int iy) { return in[ix * n + iy]; }, NoMid(),
+        [&](int ix, int iy, C2 v) { out[ix * n + iy] = v; });
+    row_pass<n, 1, false, 0>(
+        sm, tw, [&](int ix, int iy) { return out[ix * n + iy]; }, NoMid(),
+        [&](int ix, int iy, C2 v) { out[ix * n + iy] = v; });
+  }
+  const C2* wf0 = wfine + (size_t)c * 2 * P;
+  const C2* wf1 = wf0 + P;
+  const T* K2 = K2acc + (size_t)c * P;
+  C2* nuc = nu + (size_t)c * 2 * P;
+  T* nufc = nuf + (size_t)c * P;
+  C2* muDc = muD + (size_t)c * 2 * P;
+  T* muK2c = muK2 + (size_t)c * P;
+  C2* mu4c = mu4 + (size_t)c * 2 * P;
+  C2* mu3c = mu3 + (size_t)c * 2 * P;
+  const double tp = 2.0 * kPi;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const double m0 = MU[i].x, m1 = MU[i].y, m2 = MU[P + i].x, m3 = MU[P + i].y;
+    const double w0 = wf0[i].x, w1 = wf0[i].y, w2 = wf1[i].x, w3 = wf1[i].y;
+    const double D1 = DK[i].x, D2 = DK[i].y, D3 = DK[P + i].x;
+    const double K40 = DK[2 * P + i].x, K41 = -(double)DK[2 * P + i].y;
+    const double K42 = -(double)DK[3 * P + i].x, K43 = -(double)DK[3 * P + i].y;
+    const double k2 = K2[i];
+    // C0 = 2pi[K2(1-w0) - K3_0 + w0 K4_0 + w.K4];  C_c = -2 (D x w)_c + 2pi[-K2 w_c - K3_c + w0 K4_c + K4_0 w_c]
+    const double g0 = tp * (m0 * (K40 - k2) + m1 * K41 + m2 * K42 + m3 * K43);
+    // -2 (mu x D)_c + 2 pi (m0 K4_c + m_c (K4_0 - K2))
+    const double g1 = -2.0 * (m2 * D3 - m3 * D2) + tp * (m0 * K41 + m1 * (K40 - k2));
+    const double g2 = -2.0 * (m3 * D1 - m1 * D3) + tp * (m0 * K42 + m2 * (K40 - k2));
+    const double g3 = -2.0 * (m1 * D2 - m2 * D1) + tp * (m0 * K43 + m3 * (K40 - k2));
+    nuc[i] = mk2((T)g0, (T)g1);
+    nuc[P + i] = mk2((T)g2, (T)g3);
+    nufc[i] = (T)0;
+    // muD = -2 (w x mu)
+    const double dd1 = -2.0 * (w2 * m3 - w3 * m2), dd2 = -2.0 * (w3 * m1 - w1 * m3), dd3 = -2.0 * (w1 * m2 - w2 * m1);
+    muDc[i] = mk2((T)dd1, (T)dd2);
+    muDc[P + i] = mk2((T)dd3, (T)0);
+    muK2c[i] = (T)(tp * (m0 * (1.0 - w0) - m1 * w1 - m2 * w2 - m3 * w3));
+    // K4_b = eta_b raw_b
+    const double q0 = tp * (m0 * w0 + m1 * w1 + m2 * w2 + m3 * w3);
+    const double q1 = -tp * (m0 * w1 + m1 * w0), q2 = -tp * (m0 * w2 + m2 * w0), q3 = -tp * (m0 * w3 + m3 * w0);
+    mu4c[i] = mk2((T)q0, (T)q1);
+    mu4c[P + i] = mk2((T)q2, (T)q3);
+    // K3_b = eta_b raw_b, C_b has -2 pi K3_b
+    mu3c[i] = mk2((T)(-tp * m0), (T)(tp * m1));
+    mu3c[P + i] = mk2((T)(tp * m2), (T)(tp * m3));
+  }
+}
+
+// --------------------------------------------------------------------------
+// I1 transpose.  D_b = -K'(f A w_b) with A = "multiply by i phi'_j'", K' = "by i K_j'":
+//   nu_f += sum_j' (K' mu_b)(A w_b),   nu_b += -A(f K' mu_b).  One block per cell.
+// --------------------------------------------------------------------------
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads) k_i1_vjp(
+    const typename Vec2Of<T>::type* what, const typename Vec2Of<T>::type* wfine,
+    const typename Vec2Of<T>::type* muD, typename Vec2Of<T>::type* nu, T* nuf, typename Vec2Of<T>::type* ws,
+    const typename Vec2Of<T>::type* __restrict__ gtw, const T* __restrict__ phip, const T* __restrict__ Ktab,
+    int J) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
+  load_twiddles<n>(tw, gtw);
+  constexpr int P = n * n;
+  const int c = blockIdx.x;
+  C2* slot = ws + (size_t)blockIdx.x * 3 * P;
+  C2* Aw = slot;          // A w_pair
+  C2* Bm = slot + P;      // K' mu_pair
+  C2* G = slot + 2 * P;
+  const C2* wf0 = wfine + (size_t)c * 2 * P;
+  C2* nuc = nu + (size_t)c * 2 * P;
+  T* nufc = nuf + (size_t)c * P;
+  const T invP = (T)(1.0 / (double)P);
+  for (int jp = 0; jp < J; ++jp) {
+    const T* ph = phip + (size_t)jp * P;
+    const T* K = Ktab + (size_t)jp * P;
+    for (int p = 0; p < 2; ++p) {
+      const C2* in = what + ((size_t)c * 4 + 2 + p) * P;
+      const C2* mu = muD + ((size_t)c * 2 + p) * P;
+      // Aw = IFFT(i phi' w^)
+      col_pass<n, 1, false, 0>(
+          sm, tw, [&](int ix, int iy) { return mul_i(in[ix * n + iy], ph[ix * n + iy]); }, NoMid(),
+          [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+      row_pass<n, 1, false, 0>(
+          sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+          [&](int ix, int iy, C2 v) { Aw[ix * n + iy] = v; });
+      // Bm = IFFT(i K FFT(mu))   (K already carries 1/n^2)
+      row_pass<n, -1, false, 0>(
+          sm, tw, [&](int ix, int iy) { return mu[ix * n + iy]; }, NoMid(),
+          [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+      col_pass<n, -1, true, 1>(
+          sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
+          [&](int ix, int iy, C2 v) { return mul_i(v, K[ix * n + iy]); },
+          [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+      row_pass<n, 1, false, 0>(
+          sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+          [&](int ix, int iy, C2 v) { Bm[ix * n + iy] = v; });
+      // nu_f += Re.Re + Im.Im ;  then -A(f Bm) into nu (pair layout of this p)
+      row_pass<n, -1, false, 0>(
+          sm, tw,
+          [&](int ix, int iy) {
+            const int i = ix * n + iy;
+            const C2 a = Aw[i], b = Bm[i];
+            nufc[i] += a.x * b.x + a.y * b.y;
+            return cscale(b, (T)2 * wf0[i].x - (T)1);
+          },
+          NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+      col_pass<n, -1, true, 1>(
+          sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
+          [&](int ix, int iy, C2 v) { return mul_i(v, -ph[ix * n + iy] * invP); },
+          [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+      row_pass<n, 1, false, 0>(
+          sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+          [&](int ix, int iy, C2 v) {
+            const int i = ix * n + iy;
+            // pair p = 0 carries components (1, 2) -> nu pair 0 .y and nu pair 1 .x; p = 1 carries (3, -)
+            if (p == 0) {
+              nuc[i].y += v.x;
+              nuc[P + i].x += v.y;
+            } else {
+              nuc[P + i].y += v.x;
+            }
+          });
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// I2/I4 transpose.  F_{a,j} = Psi_j w_a (even multipliers: self-adjoint).
+//   K2 = 2 (pi/J) sum_{j<J/2} sum_a eta_a F_{a,j} F_{a,j'} ,  j' = j + J/2
+//   K4raw_b = (pi/J) sum_{j<J/2} [Psi_j(f F_{b,j'}) + Psi_j'(f F_{b,j})]
+// One block per cell.
+// --------------------------------------------------------------------------
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads) k_i24_vjp(
+    const typename Vec2Of<T>::type* what, const typename Vec2Of<T>::type* wfine, const T* muK2,
+    const typename Vec2Of<T>::type* mu4, typename Vec2Of<T>::type* nu, T* nuf, typename Vec2Of<T>::type* ws,
+    const typename Vec2Of<T>::type* __restrict__ gtw, const T* __restrict__ psi, int J) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
+  load_twiddles<n>(tw, gtw);
+  constexpr int P = n * n;
+  const int c = blockIdx.x;
+  C2* slot = ws + (size_t)blockIdx.x * 7 * P;
+  C2* FA = slot;             // [2] F_{.,j}
+  C2* FB = slot + 2 * P;     // [2] F_{.,j'}
+  C2* PM = slot + 4 * P;     // [2] Psi(mu4) for the current direction
+  C2* G = slot + 6 * P;
+  const C2* wf0 = wfine + (size_t)c * 2 * P;
+  const T* mk2c = muK2 + (size_t)c * P;
+  const C2* m4 = mu4 + (size_t)c * 2 * P;
+  C2* nuc = nu + (size_t)c * 2 * P;
+  T* nufc = nuf + (size_t)c * P;
+  const T wj = (T)(kPi / J);
+  const T invP = (T)(1.0 / (double)P);
+  for (int j = 0; j < J / 2; ++j) {
+    const int jq = j + J / 2;
+    for (int p = 0; p < 2; ++p) {
+      const C2* in = what + ((size_t)c * 4 + p) * P;
+      for (int h = 0; h < 2; ++h) {
+        const T* ps = psi + (size_t)(h == 0 ? j : jq) * P;
+        C2* F = (h == 0 ? FA : FB) + (size_t)p * P;
+        col_pass<n, 1, false, 0>(
+            sm, tw, [&](int ix, int iy) { return cscale(in[ix * n + iy], ps[ix * n + iy]); }, NoMid(),
+            [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+        row_pass<n, 1, false, 0>(
+            sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+            [&](int ix, int iy, C2 v) { F[ix * n + iy] = v; });
+      }
+    }
+    for (int h = 0; h < 2; ++h) {
+      const T* ps = psi + (size_t)(h == 0 ? j : jq) * P;       // Psi_j pairs with F_{j'}, Psi_j' with F_j
+      const T* pq = psi + (size_t)(h == 0 ? jq : j) * P;
+      const C2* Fo = (h == 0 ? FB : FA);                          // the other direction's F
+      for (int p = 0; p < 2; ++p) {
+        const C2* F = Fo + (size_t)p * P;
+        const C2* mup = m4 + (size_t)p * P;
+        C2* PMp = PM + (size_t)p * P;
+        const T eta0 = (p == 0) ? (T)1 : (T)-1;
+        // K2 part: nu_a += 2 (pi/J) eta_a Psi_{dir}(muK2 * F_other)
+        // K4 part: PMp = Psi_{dir}(mu4_pair)
+        for (int part = 0; part < 2; ++part) {
+          row_pass<n, -1, false, 0>(
+              sm, tw,
+              [&](int ix, int iy) {
+                const int i = ix * n + iy;
+                return part == 0 ? cscale(F[i], mk2c[i]) : mup[i];
+              },
+              NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+          col_pass<n, -1, true, 1>(
+              sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
+              [&](int ix, int iy, C2 v) { return cscale(v, ps[ix * n + iy] * invP); },
+              [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+          row_pass<n, 1, false, 0>(
+              sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+              [&](int ix, int iy, C2 v) {
+                const int i = ix * n + iy;
+                if (part == 0) {
+                  C2 o = nuc[(size_t)p * P + i];
+                  o.x += (T)2 * wj * eta0 * v.x;     // eta of component 2p
+                  o.y += (T)2 * wj * (T)(-1) * v.y;  // eta of component 2p+1 (always -1)
+                  nuc[(size_t)p * P + i] = o;
+                } else {
+                  PMp[i] = v;
+                }
+              });
+        }
+        // nu_f += (pi/J) PM . F_other ; nu_b += (pi/J) Psi_other(f PM)
+        row_pass<n, -1, false, 0>(
+            sm, tw,
+            [&](int ix, int iy) {
+              const int i = ix * n + iy;
+              const C2 pmv = PMp[i], fv = F[i];
+              nufc[i] += wj * (pmv.x * fv.x + pmv.y * fv.y);
+              return cscale(pmv, (T)2 * wf0[i].x - (T)1);
+            },
+            NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+        col_pass<n, -1, true, 1>(
+            sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
+            [&](int ix, int iy, C2 v) { return cscale(v, pq[ix * n + iy] * invP); },
+            [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+        row_pass<n, 1, false, 0>(
+            sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+            [&](int ix, int iy, C2 v) {
+              const int i = ix * n + iy;
+              C2 o = nuc[(size_t)p * P + i];
+              o.x += wj * v.x;
+              o.y += wj * v.y;
+              nuc[(size_t)p * P + i] = o;
+            });
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// I3 transpose (Hu-Ying term).  K3raw_b = sum_{j,m} sum_a eta_a S(w_a) T_ab,
+// T_ab = Psi'(w_a S(w_b)), with cotangents mu_b of K3raw_b:
+//   (i)   nu_a += S^T(eta_a sum_b mu_b T_ab)
+//   (ii)  nu_a += eta_a sum_b Q_ab S(w_b),        Q_ab = Psi'(mu_b S(w_a))
+//   (iii) nu_b += S^T(sum_a eta_a w_a Q_ab)
+// (i) and (iii) are summed before one forward FFT and accumulated in Fourier
+// space with the conjugate phase; (ii) is accumulated in real space.
+// Persistent blocks over units (cell, j, m-chunk); per unit outputs a real
+// partial [2][P] and a spectral partial [2][P].
+// --------------------------------------------------------------------------
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
+    const typename Vec2Of<T>::type* what, const typename Vec2Of<T>::type* wfine,
+    const typename Vec2Of<T>::type* mu3, typename Vec2Of<T>::type* part_r, typename Vec2Of<T>::type* part_s,
+    typename Vec2Of<T>::type* ws, const typename Vec2Of<T>::type* __restrict__ gtw,
+    const T* __restrict__ psip_s, const typename Vec2Of<T>::type* __restrict__ phase, int J, int M, int nmc, int mch,
+    int nunits) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
+  __shared__ int xcols[n];
+  __shared__ unsigned char xmask[n];
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int pos = 0; pos < n; ++pos) {
+      const int k = freq_of_pos<n>(pos);
+      const bool in = (k < n / 4) || (k >= n - n / 4);
+      xmask[pos] = in ? 1 : 0;
+      if (in) xcols[cnt++] = pos;
+    }
+  }
+  load_twiddles<n>(tw, gtw);
+  constexpr int P = n * n;
+  C2* slot = ws + (size_t)blockIdx.x * 9 * P;
+  C2* Sig = slot;            // [2] shifted pairs
+  C2* Tp = slot + 2 * P;     // [2] T_{a, pair}
+  C2* Qp = slot + 4 * P;     // [2] Q_{a, pair}
+  C2* XZ = slot + 6 * P;     // [2] (i)+(iii) real-space terms, pairs by component
+  C2* G = slot + 8 * P;
+  for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    const int c = unit / (J * nmc);
+    const int j = (unit / nmc) % J;
+    const int mc = unit % nmc;
+    C2* accr = part_r + (size_t)unit * 2 * P;
+    C2* accs = part_s + (size_t)unit * 2 * P;
+    zero_fields(accr, 2 * P);
+    zero_fields(accs, 2 * P);
+    const T* psp = psip_s + (size_t)j * P;
+    const C2* wf = wfine + (size_t)c * 2 * P;
+    const C2* mu = mu3 + (size_t)c * 2 * P;
+    const int m0 = mc * mch, m1 = min(M, m0 + mch);
+    for (int m = m0; m < m1; ++m) {
+      const C2* px = phase + ((size_t)j * M + m) * 2 * n;
+      const C2* py = px + n;
+      for (int p = 0; p < 2; ++p) {
+        const C2* in = what + ((size_t)c * 4 + p) * P;
+        C2* S = Sig + (size_t)p * P;
+        col_pass_list<n, 1, false, 0>(
+            sm, tw, xcols, n / 2,
+            [&](int ix, int iy) { return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<T>(); },
+            NoMid(), [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
+        row_pass<n, 1, false, 0>(
+            sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : zero2<T>(); }, NoMid(),
+            [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
+      }
+      zero_fields(XZ, 2 * P);
+      for (int a = 0; a < 4; ++a) {
+        const C2* wa = wf + (size_t)(a >> 1) * P;
+        const C2* Sa = Sig + (size_t)(a >> 1) * P;
+        const bool im = (a & 1) != 0;
+        const T eta_a = (a == 0) ? (T)1 : (T)-1;
+        for (int p = 0; p < 2; ++p) {
+          const C2* Sp = Sig + (size_t)p * P;
+          const C2* mup = mu + (size_t)p * P;
+          for (int which = 0; which < 2; ++which) {   // 0: T = Psi'(w_a S_pair); 1: Q = Psi'(S_a mu_pair)
+            C2* dst = (which == 0 ? Tp : Qp) + (size_t)p * P;
+            row_pass<n, -1, false, 0>(
+                sm, tw,
+                [&](int ix, int iy) {
+                  const int i = ix * n + iy;
+                  if (which == 0) {
+                    const C2 z = wa[i];
+                    return cscale(Sp[i], im ? z.y : z.x);
+                  }
+                  const C2 s = Sa[i];
+                  return cscale(mup[i], im ? s.y : s.x);
+                },
+                NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+            col_conv_pass<n>(
+                sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
+                [&](int ix, int iy) { return psp[ix * n + iy]; },
+                [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+            row_pass<n, 1, false, 0>(
+                sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+                [&](int ix, int iy, C2 v) { dst[ix * n + iy] = v; });
+          }
+        }
+        // pointwise: (i) X_a = eta_a sum_b mu_b T_ab ; (ii) Y_a = eta_a sum_b Q_ab S_b ; (iii) Z_b += eta_a w_a Q_ab
+        C2* accr_a = accr + (size_t)(a >> 1) * P;
+        C2* XZ_a = XZ + (size_t)(a >> 1) * P;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          const C2 t0 = Tp[i], t1 = Tp[P + i], q0 = Qp[i], q1 = Qp[P + i];
+          const C2 m0v = mu[i], m1v = mu[P + i];
+          const C2 s0 = Sig[i], s1 = Sig[P + i];
+          const C2 wz = wa[i];
+          const T wv = im ? wz.y : wz.x;
+          const T X = eta_a * (m0v.x * t0.x + m0v.y * t0.y + m1v.x * t1.x + m1v.y * t1.y);
+          const T Y = eta_a * (q0.x * s0.x + q0.y * s0.y + q1.x * s1.x + q1.y * s1.y);
+          if (im) {
+            accr_a[i].y += Y;
+            XZ_a[i].y += X;
+          } else {
+            accr_a[i].x += Y;
+            XZ_a[i].x += X;
+          }
+          const T e = eta_a * wv;
+          XZ[i].x += e * q0.x;
+          XZ[i].y += e * q0.y;
+          XZ[P + i].x += e * q1.x;
+          XZ[P + i].y += e * q1.y;
+        }
+        __syncthreads();
+      }
+      // S^T: forward FFT of the XZ pairs, times the conjugate phase, accumulate in Fourier space
+      for (int p = 0; p < 2; ++p) {
+        const C2* src = XZ + (size_t)p * P;
+        C2* dst = accs + (size_t)p * P;
+        row_pass<n, -1, false, 0>(
+            sm, tw, [&](int ix, int iy) { return src[ix * n + iy]; }, NoMid(),
+            [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+        col_pass<n, -1, false, 0>(
+            sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+            [&](int ix, int iy, C2 v) {
+              const C2 ph = cmul(px[ix], py[iy]);
+              const C2 z = cmulc(v, ph);
+              C2 d = dst[ix * n + iy];
+              d.x += z.x;
+              d.y += z.y;
+              dst[ix * n + iy] = d;
+            });
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Final: nu = direct + I1 + I2/I4 + 2 nu_f (into w0) + sum of the I3 real
+// partials + IFFT(sum of the I3 spectral partials / n^2); gradient = 4 E P nu.
+// One block per cell; writes grad[c][4][N][N] (FP64).
+// --------------------------------------------------------------------------
+template <int n, class T>
+__global__ void __launch_bounds__(kThreads) k_vjp_final(
+    const typename Vec2Of<T>::type* nu, const T* nuf, const typename Vec2Of<T>::type* part_r,
+    const typename Vec2Of<T>::type* part_s, int nparts, typename Vec2Of<T>::type* ws,
+    const typename Vec2Of<T>::type* __restrict__ gtw, double* grad, int accumulate) {
+  using C2 = typename Vec2Of<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* sm = tw + n;
+  load_twiddles<n>(tw, gtw);
+  constexpr int N = n / 2, P = n * n;
+  const int c = blockIdx.x;
+  C2* slot = ws + (size_t)blockIdx.x * 4 * P;
+  C2* V = slot;            // [2] total cotangent pairs
+  C2* H = slot + 2 * P;    // [2] spectral sum
+  const C2* pr = part_r + (size_t)c * nparts * 2 * P;
+  const C2* ps = part_s + (size_t)c * nparts * 2 * P;
+  for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) {
+    double sx = 0, sy = 0, hx = 0, hy = 0;
+    for (int u = 0; u < nparts; ++u) {
+      const C2 a = pr[(size_t)u * 2 * P + i], b = ps[(size_t)u * 2 * P + i];
+      sx += (double)a.x; sy += (double)a.y; hx += (double)b.x; hy += (double)b.y;
+    }
+    const C2 d = nu[(size_t)c * 2 * P + i];
+    double vx = (double)d.x + sx, vy = (double)d.y + sy;
+    if (i < P) vx += 2.0 * (double)nuf[(size_t)c * P + i];
+    V[i] = mk2((T)vx, (T)vy);
+    H[i] = mk2((T)hx, (T)hy);
+  }
+  __syncthreads();
+  const T invP = (T)(1.0 / (double)P);
+  for (int p = 0; p < 2; ++p) {
+    C2* Vp = V + (size_t)p * P;
+    C2* Hp = H + (size_t)p * P;
+    // spectral partials (permuted order) back to real space, added to V
+    col_pass<n, 1, false, 0>(
+        sm, tw, [&](int ix, int iy) { return Hp[ix * n + iy]; }, NoMid(),
+        [&](int ix, int iy, C2 v) { Hp[ix * n + iy] = v; });
+    row_pass<n, 1, false, 0>(
+        sm, tw, [&](int ix, int iy) { return Hp[ix * n + iy]; }, NoMid(),
+        [&](int ix, int iy, C2 v) {
+          C2 o = Vp[ix * n + iy];
+          o.x += v.x * invP;
+          o.y += v.y * invP;
+          Vp[ix * n + iy] = o;
+        });
+    // 4 E P V
+    row_pass<n, -1, false, 0>(
+        sm, tw, [&](int ix, int iy) { return Vp[ix * n + iy]; }, NoMid(),
+        [&](int ix, int iy, C2 v) { Hp[ix * n + iy] = v; });
+    col_pass<n, -1, true, 1>(
+        sm, tw, [&](int ix, int iy) { return Hp[ix * n + iy]; },
+        [&](int ix, int iy, C2 v) {
+          const bool keep = in_xi<n>(freq_of_pos<n>(ix)) && in_xi<n>(freq_of_pos<n>(iy));
+          return keep ? cscale(v, invP) : zero2<T>();
+        },
+        [&](int ix, int iy, C2 v) { Hp[ix * n + iy] = v; });
+    double* g = grad + (size_t)c * 4 * N * N;
+    row_pass<n, 1, false, 0>(
+        sm, tw, [&](int ix, int iy) { return Hp[ix * n + iy]; }, NoMid(),
+        [&](int ix, int iy, C2 v) {
+          if (((ix | iy) & 1) == 0) {
+            const int i = ix >> 1, j = iy >> 1;
+            double* g0 = g + ((2 * p) * N + i) * N + j;
+            double* g1 = g + ((2 * p + 1) * N + i) * N + j;
+            *g0 = (accumulate ? *g0 : 0.0) + 4.0 * (double)v.x;
+            *g1 = (accumulate ? *g1 : 0.0) + 4.0 * (double)v.y;
+          }
+        });
+  }
+}
+
+}  // namespace
+
+template <int n, class T>
+void set_vjp_smem_attributes() {
+  static bool done = false;
+  if (done) return;
+  const int sm = (int)smem_bytes<n, T>();
+  cudaFuncSetAttribute(k_vjp_seed<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i1_vjp<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i24_vjp<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i3_vjp<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_vjp_final<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  done = true;
+}
+
+// Forward prep/I1/I2+I4 (the VJP needs wfine, D^, K2, K4^) then the transpose kernels.
+template <int n, class T>
+cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
+                          double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,
+                          KernelTimer* tm) {
+  using C2 = typename Vec2Of<T>::type;
+  set_smem_attributes<n, T>();
+  set_vjp_smem_attributes<n, T>();
+  const TabPtrs<T> tb = tab_ptrs<T>(t);
+  C2* what = (C2*)cw.what;
+  C2* wfine = (C2*)cw.wfine;
+  C2* Dacc = (C2*)cw.Dacc;
+  T* K2acc = (T*)cw.K2acc;
+  C2* K4acc = (C2*)cw.K4acc;
+  C2* ws = (C2*)vw.ws;
+  const size_t sm = smem_bytes<n, T>();
+  auto begin = [&](int g) { if (tm) tm->begin(g, s); };
+  auto end = [&]() { if (tm) tm->end(s); };
+  begin(KG_VJP);
+  k_prep<n, T><<<ncells, kThreads, sm, s>>>(w, what, wfine, ws, tb.tw);
+  k_i1<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, Dacc, ws, tb.tw, tb.phip, tb.Ktab, t.J);
+  k_i24<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, K2acc, K4acc, ws, tb.tw, tb.psi, t.J);
+  C2* nu = (C2*)vw.nu;
+  T* nuf = (T*)vw.nuf;
+  C2* muD = (C2*)vw.muD;
+  T* muK2 = (T*)vw.muK2;
+  C2* mu4 = (C2*)vw.mu4;
+  C2* mu3 = (C2*)vw.mu3;
+  k_vjp_seed<n, T><<<ncells, kThreads, sm, s>>>(lam, wfine, Dacc, K2acc, K4acc, nu, nuf, muD, muK2, mu4, mu3, ws,
+                                                tb.tw);
+  k_i1_vjp<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, muD, nu, nuf, ws, tb.tw, tb.phip, tb.Ktab, t.J);
+  k_i24_vjp<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, muK2, mu4, nu, nuf, ws, tb.tw, tb.psi, t.J);
+  end();
+  const int nunits = ncells * t.J * vw.nmc;
+  const int grid = nunits < vw.grid ? nunits : vw.grid;
+  begin(KG_VJP_I3);
+  k_i3_vjp<n, T><<<grid, kThreads, sm, s>>>(what, wfine, mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw, tb.psip_s,
+                                            tb.phase, t.J, t.M, vw.nmc, vw.mch, nunits);
+  end();
+  begin(KG_VJP);
+  k_vjp_final<n, T><<<ncells, kThreads, sm, s>>>(nu, nuf, (C2*)vw.part_r, (C2*)vw.part_s, t.J * vw.nmc, ws, tb.tw,
+                                                 grad, accumulate);
+  end();
+  launches += 8;
+  return cudaGetLastError();
+}
+
+template <int n, class T>
+int i3_vjp_blocks_per_sm() {
+  set_vjp_smem_attributes<n, T>();
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_vjp<n, T>, kThreads, smem_bytes<n, T>());
+  return b < 1 ? 1 : b;
+}
+
+}  // namespace qbe

@@ -69,12 +69,32 @@ struct CollisionWork {
   double* wbuf = nullptr;
 };
 
+// Extra buffers of the collision operator's vector-Jacobian product
+// (collision_vjp.cuh) for a batch of nb cells; the forward intermediates
+// (what, wfine, D, K2, K4) are recomputed into the CollisionWork of the same batch.
+struct VjpWork {
+  int prec = 0;
+  int nb = 0;
+  int nmc = 1;           // m-chunks per (cell, j) unit of the I3 transpose kernel
+  int mch = 1;
+  int grid = 0;          // persistent grid of the I3 transpose kernel
+  void* nu = nullptr;    // [nb][2][n*n] fine-grid cotangent pairs (0,1), (2,3)
+  void* nuf = nullptr;   // [nb][n*n] (real) cotangent of f = 2 w0 - 1
+  void* muD = nullptr;   // [nb][2][n*n] cotangent of D pairs (1,2), (3,-)
+  void* muK2 = nullptr;  // [nb][n*n] (real)
+  void* mu4 = nullptr;   // [nb][2][n*n] cotangent of the raw K4 pairs
+  void* mu3 = nullptr;   // [nb][2][n*n] cotangent of the raw K3 pairs
+  void* part_r = nullptr;  // [nb*J*nmc][2][n*n] I3 transpose partials, real space
+  void* part_s = nullptr;  // [nb*J*nmc][2][n*n] I3 transpose partials, Fourier space
+  void* ws = nullptr;
+};
+
 // Launch configuration helpers.
 constexpr int kThreads = 256;
 
 // Kernel groups for the per-kernel device-time accounting (qbe_kernel_time).
 enum KernelGroup { KG_PREP = 0, KG_I1 = 1, KG_I24 = 2, KG_I3 = 3, KG_ASSEMBLE = 4, KG_TRANSPORT = 5, KG_RK = 6,
-                   KG_COUNT = 7 };
+                   KG_VJP = 7, KG_VJP_I3 = 8, KG_ADJ_TRANSPORT = 9, KG_COUNT = 10 };
 
 // Brackets launches with CUDA events on their stream when enabled; the events
 // are resolved (and the stream synchronised) only in collect().
@@ -141,6 +161,21 @@ template <int n, class T>
 int i3_blocks_per_sm();
 void free_collision_work(CollisionWork& cw);
 
+// Vector-Jacobian product of the collision operator (collision_vjp.cuh):
+// grad (+)= (dC/dW)^T lam for w, lam, grad device [nb][4][N][N]; accumulate
+// selects grad += instead of grad =.  Uses cw's forward buffers as scratch.
+cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
+                        double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,
+                        KernelTimer* tm);
+cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec = 0);
+void free_vjp_work(VjpWork& vw);
+template <int n, class T>
+cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
+                          double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,
+                          KernelTimer* tm);
+template <int n, class T>
+int i3_vjp_blocks_per_sm();
+
 // Transport, precession/RK and moments (transport.cu).
 struct BoundaryDev {
   int kind = QBE_PERIODIC;
@@ -157,6 +192,20 @@ cudaError_t rk_stage1(const double* W, const double* C, const double* B, double 
                       int Nx, int N, cudaStream_t s, long long& launches, KernelTimer* tm);
 cudaError_t rk_stage2(const double* W, const double* F0, const double* C1, const double* W1, const double* B,
                       double dt, double* Wout, int Nx, int N, cudaStream_t s, long long& launches, KernelTimer* tm);
+// Adjoints (transport.cu): the transpose of one transport substep at the
+// forward input Win (gsum: device scratch [2]); of Heun's RK2 with the
+// precession term given G1 = C'(W1)^T lam (writes lF0 and the partial lU,
+// accumulates gB); the final-time observables and their gradient.
+cudaError_t advect_substep_vjp(const double* Win, const double* lam_out, double* lam_in, int Nx, int N, double L,
+                               double tau, const BoundaryDev& bc, double* gsum, cudaStream_t s, long long& launches,
+                               KernelTimer* tm);
+cudaError_t rk_vjp_launch(const double* U, const double* W1, const double* lam, const double* G1, const double* B,
+                          double dt, double* lF0, double* lU, double* gB, int Nx, int N, cudaStream_t s,
+                          long long& launches, KernelTimer* tm);
+cudaError_t observables_launch(const double* W, int Nx, int N, double L, double* part, double* out2,
+                               cudaStream_t s, long long& launches);
+cudaError_t observables_vjp_launch(const double* gbar, int Nx, int N, double L, double* lam, cudaStream_t s,
+                                   long long& launches);
 cudaError_t moments_launch(const double* W, int Nx, int N, double L, double* out7, cudaStream_t s,
                            long long& launches);
 

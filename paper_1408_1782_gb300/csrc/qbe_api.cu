@@ -11,6 +11,30 @@
 
 using namespace qbe;
 
+namespace {
+
+// Device buffer that only grows.
+struct DevBuf {
+  double* p = nullptr;
+  size_t n = 0;   // doubles
+  cudaError_t ensure(size_t want) {
+    if (want <= n) return cudaSuccess;
+    cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc((void**)&p, want * sizeof(double));
+    if (e == cudaSuccess) n = want;
+    return e;
+  }
+  void release() {
+    cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+}  // namespace
+
 struct qbe_handle {
   qbe_grid g{};
   cudaStream_t stream = nullptr;
@@ -30,6 +54,18 @@ struct qbe_handle {
   bool has_state = false;
   long long launches = 0;
   KernelTimer timer;
+  // adjoint: collision VJP buffers (allocated on first use), the tape of the
+  // last qbe_step_checkpointed call and the reverse sweep's scratch
+  VjpWork vw;
+  bool vw_ready = false;
+  double* lbuf = nullptr;      // [nb][4][N][N] host-path staging of the cotangent
+  bool tape_valid = false;
+  double tape_dt = 0.0;
+  int tape_nsteps = 0, tape_every = 1;
+  DevBuf ckpt;                 // [ceil(nsteps/every)] states
+  DevBuf snaps;                // [every][2 sA + 2] states of one segment
+  DevBuf adj;                  // [5] states: two cotangent buffers, G1, lF0, final state
+  DevBuf small;                // gsum[2], gbar[2], obs_out[2], gB[Nx][3], obs_part[Nx][2]
 };
 
 namespace {
@@ -62,10 +98,17 @@ int transport_substeps(double tau, double dx, double L) {
   return s < 1 ? 1 : s;
 }
 
-int do_advect(qbe_handle* h, double tau) {
+// snaps (optional): receives the input state of every substep, in order.
+int do_advect(qbe_handle* h, double tau, double* snaps = nullptr) {
   const int Nx = h->g.Nx, N = h->g.N;
   const int s = transport_substeps(tau, 1.0 / Nx, h->g.L);
+  const size_t S = state_elems(h);
   for (int k = 0; k < s; ++k) {
+    if (snaps) {
+      cudaError_t e = cudaMemcpyAsync(snaps + (size_t)k * S, h->W, S * sizeof(double), cudaMemcpyDeviceToDevice,
+                                      h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "advect snapshot");
+    }
     cudaError_t e = advect_substep(h->W, h->Wa, Nx, N, h->g.L, tau / s, h->bc, h->stream, h->launches, &h->timer);
     if (e != cudaSuccess) return cuda_fail(h, e, "advect");
     std::swap(h->W, h->Wa);
@@ -84,12 +127,22 @@ int do_collide_dev(qbe_handle* h, const double* w, double* c, int ncells) {
   return QBE_OK;
 }
 
-int do_rk2(qbe_handle* h, double dt) {
+// snaps (optional): receives the stage inputs U (= W) and W1.
+int do_rk2(qbe_handle* h, double dt, double* snaps = nullptr) {
   const int Nx = h->g.Nx, N = h->g.N;
+  const size_t S = state_elems(h);
+  if (snaps) {
+    cudaError_t e = cudaMemcpyAsync(snaps, h->W, S * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rk snapshot");
+  }
   int r = do_collide_dev(h, h->W, h->Cb, Nx);
   if (r) return r;
   cudaError_t e = rk_stage1(h->W, h->Cb, h->B, dt, h->F0, h->Wa, Nx, N, h->stream, h->launches, &h->timer);
   if (e != cudaSuccess) return cuda_fail(h, e, "rk stage 1");
+  if (snaps) {
+    e = cudaMemcpyAsync(snaps + S, h->Wa, S * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rk snapshot");
+  }
   r = do_collide_dev(h, h->Wa, h->Cb, Nx);
   if (r) return r;
   e = rk_stage2(h->W, h->F0, h->Cb, h->Wa, h->B, dt, h->W, Nx, N, h->stream, h->launches, &h->timer);
@@ -97,12 +150,83 @@ int do_rk2(qbe_handle* h, double dt) {
   return QBE_OK;
 }
 
-int do_step(qbe_handle* h, double dt) {
-  int r = do_advect(h, 0.5 * dt);
-  if (!r) r = do_rk2(h, dt);
-  if (!r) r = do_advect(h, 0.5 * dt);
+// Substeps of each transport half step (the same count do_advect uses).
+int half_substeps(const qbe_handle* h, double dt) { return transport_substeps(0.5 * dt, 1.0 / h->g.Nx, h->g.L); }
+
+// snaps (optional): the 2 sA + 2 intermediate states of the step, in order
+// (inputs of the first half's substeps, U, W1, inputs of the second half's substeps).
+int do_step(qbe_handle* h, double dt, double* snaps = nullptr) {
+  const int sA = half_substeps(h, dt);
+  const size_t S = state_elems(h);
+  int r = do_advect(h, 0.5 * dt, snaps);
+  if (!r) r = do_rk2(h, dt, snaps ? snaps + (size_t)sA * S : nullptr);
+  if (!r) r = do_advect(h, 0.5 * dt, snaps ? snaps + (size_t)(sA + 2) * S : nullptr);
   return r;
 }
+
+int ensure_vjp(qbe_handle* h) {
+  if (h->vw_ready) return QBE_OK;
+  cudaError_t e = alloc_vjp_work(h->tab, h->cw.nb, h->vw, h->g.precision);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&h->lbuf, (size_t)h->cw.nb * 4 * h->g.N * h->g.N * sizeof(double));
+  if (e != cudaSuccess) {
+    free_vjp_work(h->vw);
+    cudaFree(h->lbuf);
+    h->lbuf = nullptr;
+    return fail(h, QBE_ERR_ALLOC, std::string("adjoint workspace: ") + cudaGetErrorString(e));
+  }
+  h->vw_ready = true;
+  return QBE_OK;
+}
+
+int do_collide_vjp_dev(qbe_handle* h, const double* w, const double* lam, double* grad, int ncells, int accumulate) {
+  int r = ensure_vjp(h);
+  if (r) return r;
+  const size_t per = (size_t)4 * h->g.N * h->g.N;
+  for (int c0 = 0; c0 < ncells; c0 += h->cw.nb) {
+    const int nc = (ncells - c0) < h->cw.nb ? (ncells - c0) : h->cw.nb;
+    cudaError_t e = collide_vjp(h->tab, h->cw, h->vw, w + (size_t)c0 * per, lam + (size_t)c0 * per,
+                                grad + (size_t)c0 * per, nc, accumulate, h->stream, h->launches, &h->timer);
+    if (e != cudaSuccess) return cuda_fail(h, e, "collide vjp");
+  }
+  return QBE_OK;
+}
+
+// Reverse of one recorded step: *lam (cotangent of the step's output) becomes
+// the cotangent of its input; gB accumulates the field gradient.  *lam and
+// *tmp are swapped as the sweep ping-pongs between them.
+int step_vjp_one(qbe_handle* h, double dt, const double* snaps, double** lam, double** tmp, double* G1, double* lF0,
+                 double* gB, double* gsum) {
+  const int Nx = h->g.Nx, N = h->g.N;
+  const int sA = half_substeps(h, dt);
+  const double tau = 0.5 * dt / sA;
+  const size_t S = state_elems(h);
+  for (int k = sA - 1; k >= 0; --k) {
+    cudaError_t e = advect_substep_vjp(snaps + (size_t)(sA + 2 + k) * S, *lam, *tmp, Nx, N, h->g.L, tau, h->bc,
+                                       gsum, h->stream, h->launches, &h->timer);
+    if (e != cudaSuccess) return cuda_fail(h, e, "advect vjp");
+    std::swap(*lam, *tmp);
+  }
+  const double* U = snaps + (size_t)sA * S;
+  const double* W1 = snaps + (size_t)(sA + 1) * S;
+  int r = do_collide_vjp_dev(h, W1, *lam, G1, Nx, 0);
+  if (r) return r;
+  cudaError_t e = rk_vjp_launch(U, W1, *lam, G1, h->B, dt, lF0, *tmp, gB, Nx, N, h->stream, h->launches,
+                                &h->timer);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rk vjp");
+  r = do_collide_vjp_dev(h, U, lF0, *tmp, Nx, 1);
+  if (r) return r;
+  std::swap(*lam, *tmp);
+  for (int k = sA - 1; k >= 0; --k) {
+    e = advect_substep_vjp(snaps + (size_t)k * S, *lam, *tmp, Nx, N, h->g.L, tau, h->bc, gsum, h->stream,
+                           h->launches, &h->timer);
+    if (e != cudaSuccess) return cuda_fail(h, e, "advect vjp");
+    std::swap(*lam, *tmp);
+  }
+  return QBE_OK;
+}
+
+size_t small_elems(const qbe_handle* h) { return 6 + (size_t)h->g.Nx * 5; }
 
 bool valid_fd(const qbe_fd* f) {
   return f && std::isfinite(f->beta) && f->beta > 0 && std::isfinite(f->mu_up) && std::isfinite(f->mu_dn);
@@ -169,6 +293,9 @@ void qbe_destroy(qbe_handle* h) {
   free_collision_work(h->cw);
   cudaFree(h->W); cudaFree(h->Wa); cudaFree(h->F0); cudaFree(h->Cb); cudaFree(h->B);
   cudaFree(h->mom); cudaFree(h->fbar); cudaFree(h->phiL); cudaFree(h->phiR);
+  free_vjp_work(h->vw);
+  cudaFree(h->lbuf);
+  h->ckpt.release(); h->snaps.release(); h->adj.release(); h->small.release();
   delete h;
 }
 
@@ -206,6 +333,7 @@ int qbe_set_boundary(qbe_handle* h, int bc, const qbe_fd* left, const qbe_fd* ri
   if (bc != QBE_PERIODIC && bc != QBE_DIRICHLET && bc != QBE_MAXWELL)
     return fail(h, QBE_ERR_ARG, "unknown boundary kind");
   DeviceGuard dg(h->g.device);
+  h->tape_valid = false;
   if (bc == QBE_PERIODIC) {
     h->bc.kind = bc;
     return QBE_OK;
@@ -245,6 +373,7 @@ int qbe_set_bfield(qbe_handle* h, const double* B, int on_device) {
   if (!h || !B) return h ? fail(h, QBE_ERR_ARG, "null B") : QBE_ERR_ARG;
   DeviceGuard dg(h->g.device);
   const size_t bytes = (size_t)h->g.Nx * 3 * sizeof(double);
+  h->tape_valid = false;
   cudaError_t e = cudaMemcpyAsync(h->B, B, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                   h->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
@@ -254,6 +383,7 @@ int qbe_set_bfield(qbe_handle* h, const double* B, int on_device) {
 int qbe_set_state(qbe_handle* h, const double* w, int on_device) {
   if (!h || !w) return h ? fail(h, QBE_ERR_ARG, "null state") : QBE_ERR_ARG;
   DeviceGuard dg(h->g.device);
+  h->tape_valid = false;
   cudaError_t e = cudaMemcpyAsync(h->W, w, state_elems(h) * sizeof(double),
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
@@ -298,6 +428,7 @@ int qbe_advect(qbe_handle* h, double tau) {
   if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
   if (!std::isfinite(tau)) return fail(h, QBE_ERR_ARG, "tau not finite");
   DeviceGuard dg(h->g.device);
+  h->tape_valid = false;
   return do_advect(h, tau);
 }
 
@@ -306,6 +437,7 @@ int qbe_collide_rk2(qbe_handle* h, double dt) {
   if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
   if (!std::isfinite(dt)) return fail(h, QBE_ERR_ARG, "dt not finite");
   DeviceGuard dg(h->g.device);
+  h->tape_valid = false;
   return do_rk2(h, dt);
 }
 
@@ -314,6 +446,7 @@ int qbe_step(qbe_handle* h, double dt, int nsteps) {
   if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
   if (!std::isfinite(dt) || nsteps < 0) return fail(h, QBE_ERR_ARG, "bad dt or nsteps");
   DeviceGuard dg(h->g.device);
+  h->tape_valid = false;
   for (int s = 0; s < nsteps; ++s) {
     const int r = do_step(h, dt);
     if (r) return r;
@@ -344,6 +477,153 @@ int qbe_moments(qbe_handle* h, double* rho, double* mom, double* energy, int on_
   if (e == cudaSuccess && mom) e = cudaMemcpy(mom, m2.data(), m2.size() * sizeof(double), k);
   if (e == cudaSuccess && energy) e = cudaMemcpy(energy, en.data(), en.size() * sizeof(double), k);
   return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "moments copy");
+}
+
+int qbe_collide_vjp(qbe_handle* h, const double* w, const double* lam, double* grad, int ncells, int on_device) {
+  if (!h) return QBE_ERR_ARG;
+  if (!w || !lam || !grad || ncells < 1) return fail(h, QBE_ERR_ARG, "collide_vjp: null pointer or ncells < 1");
+  DeviceGuard dg(h->g.device);
+  if (on_device) return do_collide_vjp_dev(h, w, lam, grad, ncells, 0);
+  int r = ensure_vjp(h);
+  if (r) return r;
+  const size_t per = (size_t)4 * h->g.N * h->g.N;
+  for (int c0 = 0; c0 < ncells; c0 += h->cw.nb) {
+    const int nc = (ncells - c0) < h->cw.nb ? (ncells - c0) : h->cw.nb;
+    const size_t bytes = (size_t)nc * per * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(h->cw.wbuf, w + (size_t)c0 * per, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->lbuf, lam + (size_t)c0 * per, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "collide_vjp H2D");
+    r = do_collide_vjp_dev(h, h->cw.wbuf, h->lbuf, h->cw.cbuf, nc, 0);
+    if (r) return r;
+    e = cudaMemcpyAsync(grad + (size_t)c0 * per, h->cw.cbuf, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "collide_vjp D2H");
+  }
+  return QBE_OK;
+}
+
+int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_every) {
+  if (!h) return QBE_ERR_ARG;
+  if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
+  if (!std::isfinite(dt) || nsteps < 1 || checkpoint_every < 1)
+    return fail(h, QBE_ERR_ARG, "bad dt, nsteps or checkpoint_every");
+  DeviceGuard dg(h->g.device);
+  h->tape_valid = false;
+  const size_t S = state_elems(h);
+  const int every = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+  const size_t nck = (size_t)(nsteps + every - 1) / every;
+  cudaError_t e = h->ckpt.ensure(nck * S);
+  if (e != cudaSuccess) return fail(h, QBE_ERR_ALLOC, "checkpoint storage");
+  for (int s = 0; s < nsteps; ++s) {
+    if (s % every == 0) {
+      e = cudaMemcpyAsync(h->ckpt.p + (size_t)(s / every) * S, h->W, S * sizeof(double), cudaMemcpyDeviceToDevice,
+                          h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint");
+    }
+    const int r = do_step(h, dt);
+    if (r) return r;
+  }
+  h->tape_valid = true;
+  h->tape_dt = dt;
+  h->tape_nsteps = nsteps;
+  h->tape_every = every;
+  return QBE_OK;
+}
+
+int qbe_step_vjp(qbe_handle* h, const double* lam_final, double* lam_init, double* grad_B, int on_device) {
+  if (!h) return QBE_ERR_ARG;
+  if (!lam_final || !lam_init) return fail(h, QBE_ERR_ARG, "step_vjp: null cotangent");
+  if (!h->tape_valid) return fail(h, QBE_ERR_STATE, "no valid tape (call qbe_step_checkpointed first)");
+  DeviceGuard dg(h->g.device);
+  const int Nx = h->g.Nx;
+  const double dt = h->tape_dt;
+  const int nsteps = h->tape_nsteps, every = h->tape_every;
+  const size_t S = state_elems(h);
+  const int sA = half_substeps(h, dt);
+  const size_t per_step = (size_t)(2 * sA + 2) * S;
+  int r = ensure_vjp(h);
+  if (r) return r;
+  if (h->snaps.ensure((size_t)every * per_step) != cudaSuccess || h->adj.ensure(5 * S) != cudaSuccess ||
+      h->small.ensure(small_elems(h)) != cudaSuccess)
+    return fail(h, QBE_ERR_ALLOC, "adjoint sweep storage");
+  double* lam = h->adj.p;
+  double* tmp = h->adj.p + S;
+  double* G1 = h->adj.p + 2 * S;
+  double* lF0 = h->adj.p + 3 * S;
+  double* Wfin = h->adj.p + 4 * S;
+  double* gsum = h->small.p;
+  double* gB = h->small.p + 6;
+  const size_t sb = S * sizeof(double);
+  cudaError_t e = cudaMemcpyAsync(lam, lam_final, sb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(gB, 0, (size_t)Nx * 3 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Wfin, h->W, sb, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_vjp setup");
+  const int nseg = (nsteps + every - 1) / every;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int s0 = seg * every;
+    const int len = (nsteps - s0) < every ? (nsteps - s0) : every;
+    // recompute the segment from its checkpoint, recording every step's intermediate states
+    e = cudaMemcpyAsync(h->W, h->ckpt.p + (size_t)seg * S, sb, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "restore checkpoint");
+    for (int i = 0; i < len; ++i) {
+      r = do_step(h, dt, h->snaps.p + (size_t)i * per_step);
+      if (r) return r;
+    }
+    for (int i = len - 1; i >= 0; --i) {
+      r = step_vjp_one(h, dt, h->snaps.p + (size_t)i * per_step, &lam, &tmp, G1, lF0, gB, gsum);
+      if (r) return r;
+    }
+  }
+  e = cudaMemcpyAsync(h->W, Wfin, sb, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(lam_init, lam, sb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && grad_B)
+    e = cudaMemcpyAsync(grad_B, gB, (size_t)Nx * 3 * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "step_vjp output");
+}
+
+int qbe_observables(qbe_handle* h, const double* w, double* out, int on_device) {
+  if (!h) return QBE_ERR_ARG;
+  if (!out) return fail(h, QBE_ERR_ARG, "observables: null output");
+  if (!w && !h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
+  DeviceGuard dg(h->g.device);
+  if (h->small.ensure(small_elems(h)) != cudaSuccess || h->adj.ensure(5 * state_elems(h)) != cudaSuccess)
+    return fail(h, QBE_ERR_ALLOC, "observables scratch");
+  double* o2 = h->small.p + 4;
+  double* part = h->small.p + 6 + (size_t)h->g.Nx * 3;
+  const double* src = w ? w : h->W;
+  cudaError_t e = cudaSuccess;
+  if (w && !on_device) {
+    e = cudaMemcpyAsync(h->adj.p, w, state_elems(h) * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    src = h->adj.p;
+  }
+  if (e == cudaSuccess) e = observables_launch(src, h->g.Nx, h->g.N, h->g.L, part, o2, h->stream, h->launches);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, o2, 2 * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "observables");
+}
+
+int qbe_observables_vjp(qbe_handle* h, const double* gbar, double* lam, int on_device) {
+  if (!h) return QBE_ERR_ARG;
+  if (!gbar || !lam) return fail(h, QBE_ERR_ARG, "observables_vjp: null pointer");
+  DeviceGuard dg(h->g.device);
+  if (h->small.ensure(small_elems(h)) != cudaSuccess || h->adj.ensure(5 * state_elems(h)) != cudaSuccess)
+    return fail(h, QBE_ERR_ALLOC, "observables scratch");
+  double* g2 = h->small.p + 2;
+  cudaError_t e = cudaMemcpyAsync(g2, gbar, 2 * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+  double* dst = on_device ? lam : h->adj.p;
+  if (e == cudaSuccess) e = observables_vjp_launch(g2, h->g.Nx, h->g.N, h->g.L, dst, h->stream, h->launches);
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(lam, dst, state_elems(h) * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "observables_vjp");
 }
 
 }  // extern "C"
@@ -498,6 +778,7 @@ int qbe_batch_step(qbe_batch* b, double dt, int nsteps) {
   if (!std::isfinite(dt) || nsteps < 0) return bfail(b, QBE_ERR_ARG, "bad dt or nsteps");
   for (auto h : b->sims)
     if (!h->has_state) return bfail(b, QBE_ERR_STATE, "a simulation has no state");
+  for (auto h : b->sims) h->tape_valid = false;
   DeviceGuard dg(b->device);
   if (!b->exec || b->graph_dt != dt) {
     drop_graph(b);

@@ -171,6 +171,279 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ W, i
   if (threadIdx.x < 7) out7[(size_t)cell * 7 + threadIdx.x] = red[threadIdx.x][0] * dv * dv;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the transport substep.  With the minmod branches frozen at the
+// forward state (a tie |a| = |b| takes a's branch, as in minmod above) the
+// update is linear in the five stencil values; advect_coefs returns
+// dWout(j)/dWv[d] for the output (j, c, ix, iy).  The input cotangent is
+// gathered over every output whose stencil reads the input, directly or
+// through a ghost cell: periodic wrap, the copied boundary cell (outgoing
+// velocities), the specular image (1 - alpha) W_b(-v_x, v_y) and the
+// diffusive part alpha W_FD(v) Fbar / Z with Fbar a linear functional of the
+// boundary cell's w0 (Sec. 2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int minmod_branch(double a, double b) {   // 0: zero, 1: a, 2: b
+  return (a * b > 0.0) ? (fabs(a) <= fabs(b) ? 1 : 2) : 0;
+}
+
+__device__ __forceinline__ void advect_coefs(const double* __restrict__ W, int j, int c, int ix, int iy, int Nx,
+                                             int N, double vx, double tau, double dx, const Ghost& g,
+                                             double coef[5]) {
+  double Wv[5];
+#pragma unroll
+  for (int d = 0; d < 5; ++d) Wv[d] = cell_value(W, j - 2 + d, c, ix, iy, Nx, N, vx, g);
+  const double nu = tau * vx / dx;
+  const double sg = (nu > 0.0) ? 1.0 : (nu < 0.0 ? -1.0 : 0.0);
+  const double lim = 0.5 * (sg - nu);
+  const double k = tau / (2.0 * dx);
+  const double av = fabs(vx);
+  coef[0] = 0.0;
+  coef[1] = k * (vx + av);
+  coef[2] = 1.0 - 2.0 * k * av;
+  coef[3] = k * (-vx + av);
+  coef[4] = 0.0;
+  const double cm = k * lim * (vx + av), c0 = k * lim * (-2.0 * av), cp = k * lim * (-vx + av);
+  // S_{-1} = minmod(W2 - W1, W1 - W0)
+  switch (minmod_branch(Wv[2] - Wv[1], Wv[1] - Wv[0])) {
+    case 1: coef[2] += cm; coef[1] -= cm; break;
+    case 2: coef[1] += cm; coef[0] -= cm; break;
+    default: break;
+  }
+  // S_0 = minmod(W3 - W2, W2 - W1)
+  switch (minmod_branch(Wv[3] - Wv[2], Wv[2] - Wv[1])) {
+    case 1: coef[3] += c0; coef[2] -= c0; break;
+    case 2: coef[2] += c0; coef[1] -= c0; break;
+    default: break;
+  }
+  // S_{+1} = minmod(W4 - W3, W3 - W2)
+  switch (minmod_branch(Wv[4] - Wv[3], Wv[3] - Wv[2])) {
+    case 1: coef[4] += cp; coef[3] -= cp; break;
+    case 2: coef[3] += cp; coef[2] -= cp; break;
+    default: break;
+  }
+}
+
+// Cotangent that reaches ghost cell gcell (outside [0, Nx)) at (c, ix, iy):
+// sum over outputs jo and stencil slots d with jo - 2 + d = gcell.
+__device__ __forceinline__ double ghost_cotangent(const double* __restrict__ W, const double* __restrict__ lam,
+                                                  int gcell, int c, int ix, int iy, int Nx, int N, double vx,
+                                                  double tau, double dx, const Ghost& g) {
+  const size_t NN = (size_t)N * N;
+  const size_t off = (size_t)c * NN + (size_t)ix * N + iy;
+  double acc = 0.0;
+  for (int d = 0; d < 5; ++d) {
+    const int jo = gcell + 2 - d;
+    if (jo < 0 || jo >= Nx) continue;
+    double coef[5];
+    advect_coefs(W, jo, c, ix, iy, Nx, N, vx, tau, dx, g, coef);
+    acc += lam[(size_t)jo * 4 * NN + off] * coef[d];
+  }
+  return acc;
+}
+
+// Maxwell walls: gsum[side] = sum over incoming velocities and components of
+// the ghost cotangents times W_FD (the diffusive part's dependence on Fbar).
+__global__ void __launch_bounds__(256) k_wall_adj(const double* __restrict__ W, const double* __restrict__ lam,
+                                                  int Nx, int N, double L, double tau, Ghost g, double* gsum) {
+  __shared__ double red[256];
+  const int side = blockIdx.x;
+  const int NN = N * N;
+  const double dv = 2.0 * L / N;
+  const double dx = 1.0 / Nx;
+  const double* phi = side == 0 ? g.phiL : g.phiR;
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < 4 * NN; t += blockDim.x) {
+    const int c = t / NN, ix = (t % NN) / N, iy = t % N;
+    const double vx = dv * (ix - N / 2);
+    const bool incoming = side == 0 ? (vx > 0.0) : (vx < 0.0);
+    if (!incoming) continue;
+    const int g0 = side == 0 ? -2 : Nx, g1 = side == 0 ? -1 : Nx + 1;
+    const double lg = ghost_cotangent(W, lam, g0, c, ix, iy, Nx, N, vx, tau, dx, g) +
+                      ghost_cotangent(W, lam, g1, c, ix, iy, Nx, N, vx, tau, dx, g);
+    acc += lg * phi[t];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gsum[side] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_advect_vjp(const double* __restrict__ W, const double* __restrict__ lam,
+                                                    double* __restrict__ lam_in, int Nx, int N, double L, double tau,
+                                                    Ghost g, const double* __restrict__ gsum) {
+  const size_t NN = (size_t)N * N;
+  const size_t total = (size_t)Nx * 4 * NN;
+  const double dv = 2.0 * L / N;
+  const double dx = 1.0 / Nx;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / (4 * NN));
+    const int c = (int)((t / NN) % 4);
+    const int ix = (int)((t % NN) / N);
+    const int iy = (int)(t % N);
+    const size_t off = (size_t)c * NN + (size_t)ix * N + iy;
+    const double vx = dv * (ix - N / 2);
+    double acc = 0.0;
+    for (int d = 0; d < 5; ++d) {
+      int jo = j + 2 - d;
+      if (g.kind == QBE_PERIODIC) {
+        jo = (jo % Nx + Nx) % Nx;
+      } else if (jo < 0 || jo >= Nx) {
+        continue;
+      }
+      double coef[5];
+      advect_coefs(W, jo, c, ix, iy, Nx, N, vx, tau, dx, g, coef);
+      acc += lam[(size_t)jo * 4 * NN + off] * coef[d];
+    }
+    if (g.kind != QBE_PERIODIC) {
+      for (int side = 0; side < 2; ++side) {
+        if (j != (side == 0 ? 0 : Nx - 1)) continue;
+        const int g0 = side == 0 ? -2 : Nx, g1 = side == 0 ? -1 : Nx + 1;
+        const bool incoming = side == 0 ? (vx > 0.0) : (vx < 0.0);
+        if (!incoming)   // the ghost copies this boundary value
+          acc += ghost_cotangent(W, lam, g0, c, ix, iy, Nx, N, vx, tau, dx, g) +
+                 ghost_cotangent(W, lam, g1, c, ix, iy, Nx, N, vx, tau, dx, g);
+        if (g.kind == QBE_MAXWELL) {
+          // specular image: this value feeds the ghost at velocity index N - ix when that one is incoming
+          const int mx = N - ix;
+          const double vm = -vx;
+          const bool m_in = side == 0 ? (vm > 0.0) : (vm < 0.0);
+          if (mx < N && m_in)
+            acc += (1.0 - g.alpha) * (ghost_cotangent(W, lam, g0, c, mx, iy, Nx, N, vm, tau, dx, g) +
+                                      ghost_cotangent(W, lam, g1, c, mx, iy, Nx, N, vm, tau, dx, g));
+          // diffusive part through Fbar = dv^2 sum_{outgoing} 2 w0 |v_x|
+          const bool out = side == 0 ? (vx < 0.0) : (vx > 0.0);
+          if (c == 0 && out) {
+            const double Z = side == 0 ? g.ZL : g.ZR;
+            acc += g.alpha / Z * dv * dv * 2.0 * fabs(vx) * gsum[side];
+          }
+        }
+      }
+    }
+    lam_in[t] = acc;
+  }
+}
+
+// Adjoint of Heun's method for dW/dt = C[W] + 2 (B x w).sigma (k_rk1, k_rk2).
+// Forward: F0 = C(U) + P_B U, W1 = U + dt F0, Z = U + dt/2 (F0 + C(W1) + P_B W1).
+// Given lam = dZ-cotangent and G1 = C'(W1)^T lam (one collision VJP):
+//   lW1 = dt/2 G1 + P_B^T (dt/2 lam),  lF0 = dt/2 lam + dt lW1,
+//   lU  = lam + lW1 + P_B^T lF0 + C'(U)^T lF0   (the last term by a second VJP),
+// with P_B^T mu = -2 B x mu; the B-gradient per cell is
+//   sum_v [2 W1 x (dt/2 lam) + 2 U x lF0].
+// One block per cell (the B reduction is per cell); writes lF0 and the
+// partial lU, accumulates gB[cell].
+__global__ void __launch_bounds__(256) k_rk_vjp(const double* __restrict__ U, const double* __restrict__ W1,
+                                                const double* __restrict__ lam, const double* __restrict__ G1,
+                                                const double* __restrict__ B, double dt, double* __restrict__ lF0,
+                                                double* __restrict__ lU, double* gB, int N) {
+  __shared__ double red[3][256];
+  const size_t NN = (size_t)N * N;
+  const int cell = blockIdx.x;
+  const double* b = B + 3 * cell;
+  const size_t cb = (size_t)cell * 4 * NN;
+  double gb[3] = {0, 0, 0};
+  for (size_t v = threadIdx.x; v < NN; v += blockDim.x) {
+    const size_t base = cb + v;
+    double l[4], g1[4], lw1[4], lf[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      l[c] = lam[base + c * NN];
+      g1[c] = G1[base + c * NN];
+    }
+    const double h = 0.5 * dt;
+    // P_B^T (h lam) = -2 B x (h lam)
+    lw1[0] = h * g1[0];
+    lw1[1] = h * g1[1] - 2.0 * h * (b[1] * l[3] - b[2] * l[2]);
+    lw1[2] = h * g1[2] - 2.0 * h * (b[2] * l[1] - b[0] * l[3]);
+    lw1[3] = h * g1[3] - 2.0 * h * (b[0] * l[2] - b[1] * l[1]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) lf[c] = h * l[c] + dt * lw1[c];
+    double pu[4];
+    pu[0] = 0.0;
+    pu[1] = -2.0 * (b[1] * lf[3] - b[2] * lf[2]);
+    pu[2] = -2.0 * (b[2] * lf[1] - b[0] * lf[3]);
+    pu[3] = -2.0 * (b[0] * lf[2] - b[1] * lf[1]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      lF0[base + c * NN] = lf[c];
+      lU[base + c * NN] = l[c] + lw1[c] + pu[c];
+    }
+    const double x1 = W1[base + NN], x2 = W1[base + 2 * NN], x3 = W1[base + 3 * NN];
+    const double u1 = U[base + NN], u2 = U[base + 2 * NN], u3 = U[base + 3 * NN];
+    // 2 x x (h lam) + 2 u x lF0
+    gb[0] += 2.0 * h * (x2 * l[3] - x3 * l[2]) + 2.0 * (u2 * lf[3] - u3 * lf[2]);
+    gb[1] += 2.0 * h * (x3 * l[1] - x1 * l[3]) + 2.0 * (u3 * lf[1] - u1 * lf[3]);
+    gb[2] += 2.0 * h * (x1 * l[2] - x2 * l[1]) + 2.0 * (u1 * lf[2] - u2 * lf[1]);
+  }
+  for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = gb[k];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) gB[(size_t)cell * 3 + threadIdx.x] += red[threadIdx.x][0];
+}
+
+// Final-time observables per cell: [0] = dv^2 sum 2 w3 (spin polarisation
+// along z), [1] = dv^2 sum v_x |v|^2/2 2 w0 (energy flux); times dx after the
+// fixed-order sum over cells in k_observables_sum.
+__global__ void __launch_bounds__(256) k_observables(const double* __restrict__ W, int N, double L, double* part) {
+  __shared__ double red[2][256];
+  const int cell = blockIdx.x;
+  const size_t NN = (size_t)N * N;
+  const double dv = 2.0 * L / N;
+  const double* w = W + (size_t)cell * 4 * NN;
+  double a = 0.0, e = 0.0;
+  for (size_t i = threadIdx.x; i < NN; i += blockDim.x) {
+    const int ix = (int)(i / N), iy = (int)(i % N);
+    const double vx = dv * (ix - N / 2), vy = dv * (iy - N / 2);
+    a += 2.0 * w[3 * NN + i];
+    e += vx * 0.5 * (vx * vx + vy * vy) * 2.0 * w[i];
+  }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = e;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) part[(size_t)cell * 2 + threadIdx.x] = red[threadIdx.x][0] * dv * dv;
+}
+
+__global__ void k_observables_sum(const double* __restrict__ part, int Nx, double* out) {
+  if (threadIdx.x < 2) {
+    double s = 0.0;
+    for (int j = 0; j < Nx; ++j) s += part[(size_t)j * 2 + threadIdx.x];
+    out[threadIdx.x] = s / Nx;
+  }
+}
+
+// lam = gbar[0] dP_z/dW + gbar[1] dPhi_E/dW
+__global__ void __launch_bounds__(256) k_observables_vjp(const double* __restrict__ gbar, int Nx, int N, double L,
+                                                         double* __restrict__ lam) {
+  const size_t NN = (size_t)N * N;
+  const size_t total = (size_t)Nx * 4 * NN;
+  const double dv = 2.0 * L / N;
+  const double s = dv * dv / Nx;
+  const double g0 = gbar[0], g1 = gbar[1];
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)((t / NN) % 4);
+    const int ix = (int)((t % NN) / N), iy = (int)(t % N);
+    const double vx = dv * (ix - N / 2), vy = dv * (iy - N / 2);
+    double v = 0.0;
+    if (c == 3) v = 2.0 * s * g0;
+    if (c == 0) v = s * g1 * vx * (vx * vx + vy * vy);
+    lam[t] = v;
+  }
+}
+
 int grid_for(size_t total) {
   size_t g = (total + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
@@ -215,6 +488,51 @@ cudaError_t rk_stage2(const double* W, const double* F0, const double* C1, const
 cudaError_t moments_launch(const double* W, int Nx, int N, double L, double* out7, cudaStream_t s,
                            long long& launches) {
   k_moments<<<Nx, 256, 0, s>>>(W, N, L, out7);
+  ++launches;
+  return cudaGetLastError();
+}
+
+cudaError_t advect_substep_vjp(const double* Win, const double* lam_out, double* lam_in, int Nx, int N, double L,
+                               double tau, const BoundaryDev& bc, double* gsum, cudaStream_t s,
+                               long long& launches, KernelTimer* tm) {
+  if (tm) tm->begin(KG_ADJ_TRANSPORT, s);
+  if (bc.kind == QBE_MAXWELL) {
+    k_wall_flux<<<2, 256, 0, s>>>(Win, Nx, N, L, bc.fbar);
+    ++launches;
+  }
+  Ghost g{bc.kind, bc.alpha, bc.ZL, bc.ZR, bc.phiL, bc.phiR, bc.fbar};
+  if (bc.kind == QBE_MAXWELL) {
+    k_wall_adj<<<2, 256, 0, s>>>(Win, lam_out, Nx, N, L, tau, g, gsum);
+    ++launches;
+  }
+  const size_t total = (size_t)Nx * 4 * N * N;
+  k_advect_vjp<<<grid_for(total), 256, 0, s>>>(Win, lam_out, lam_in, Nx, N, L, tau, g, gsum);
+  if (tm) tm->end(s);
+  ++launches;
+  return cudaGetLastError();
+}
+
+cudaError_t rk_vjp_launch(const double* U, const double* W1, const double* lam, const double* G1, const double* B,
+                          double dt, double* lF0, double* lU, double* gB, int Nx, int N, cudaStream_t s,
+                          long long& launches, KernelTimer* tm) {
+  if (tm) tm->begin(KG_ADJ_TRANSPORT, s);
+  k_rk_vjp<<<Nx, 256, 0, s>>>(U, W1, lam, G1, B, dt, lF0, lU, gB, N);
+  if (tm) tm->end(s);
+  ++launches;
+  return cudaGetLastError();
+}
+
+cudaError_t observables_launch(const double* W, int Nx, int N, double L, double* part, double* out2,
+                               cudaStream_t s, long long& launches) {
+  k_observables<<<Nx, 256, 0, s>>>(W, N, L, part);
+  k_observables_sum<<<1, 32, 0, s>>>(part, Nx, out2);
+  launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t observables_vjp_launch(const double* gbar, int Nx, int N, double L, double* lam, cudaStream_t s,
+                                   long long& launches) {
+  k_observables_vjp<<<grid_for((size_t)Nx * 4 * N * N), 256, 0, s>>>(gbar, Nx, N, L, lam);
   ++launches;
   return cudaGetLastError();
 }

@@ -51,6 +51,11 @@ SIGNATURES = {
     "qbe_launch_count": (ctypes.c_longlong, [_c_void_p]),
     "qbe_enable_timing": (_c_int, [_c_void_p, _c_int]),
     "qbe_kernel_time": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "qbe_collide_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int, _c_int]),
+    "qbe_step_checkpointed": (_c_int, [_c_void_p, _c_double, _c_int, _c_int]),
+    "qbe_step_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int]),
+    "qbe_observables": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int]),
+    "qbe_observables_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_collide_noalloc": (_c_int, [ctypes.POINTER(QbeGrid), _c_void_p, _c_void_p, _c_int, _c_void_p]),
     "qbe_batch_create": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, ctypes.POINTER(_c_void_p)]),
     "qbe_batch_destroy": (None, [_c_void_p]),
@@ -62,7 +67,8 @@ SIGNATURES = {
     "qbe_batch_step": (_c_int, [_c_void_p, _c_double, _c_int]),
 }
 
-KERNEL_GROUPS = {"prep": 0, "i1": 1, "i24": 2, "i3": 3, "assemble": 4, "transport": 5, "rk": 6}
+KERNEL_GROUPS = {"prep": 0, "i1": 1, "i24": 2, "i3": 3, "assemble": 4, "transport": 5, "rk": 6,
+                 "vjp": 7, "vjp_i3": 8, "adj_transport": 9}
 
 _lib = None
 
@@ -146,6 +152,8 @@ class Batch:
         return out
 
     def step(self, dt, nsteps=1):
+        for sv in self.solvers:
+            sv._gen += 1
         self._check(lib().qbe_batch_step(self._b, float(dt), int(nsteps)), "qbe_batch_step")
 
     def close(self):
@@ -193,6 +201,7 @@ class Solver:
         if rc != 0:
             raise QbeError(f"qbe_create failed with code {rc}")
         self._h = h
+        self._gen = 0   # bumped by every call that changes the state, the field or the boundary
         if stream is not None:
             self.set_stream(stream)
 
@@ -224,16 +233,19 @@ class Solver:
 
     # -- configuration ----------------------------------------------------
     def set_boundary(self, kind="periodic", left=None, right=None, alpha=0.0):
+        self._gen += 1
         k = _BC[kind] if isinstance(kind, str) else int(kind)
         lp = ctypes.byref(left) if left is not None else None
         rp = ctypes.byref(right) if right is not None else None
         self._check(lib().qbe_set_boundary(self._h, k, lp, rp, float(alpha)), "qbe_set_boundary")
 
     def set_bfield(self, B):
+        self._gen += 1
         p, dev, keep = _arg(B, (self.Nx, 3))
         self._check(lib().qbe_set_bfield(self._h, _c_void_p(p), dev), "qbe_set_bfield")
 
     def set_state(self, w):
+        self._gen += 1
         p, dev, keep = _arg(w, self.state_shape)
         self._check(lib().qbe_set_state(self._h, _c_void_p(p), dev), "qbe_set_state")
 
@@ -262,13 +274,83 @@ class Solver:
         return out
 
     def advect(self, tau):
+        self._gen += 1
         self._check(lib().qbe_advect(self._h, float(tau)), "qbe_advect")
 
     def collide_rk2(self, dt):
+        self._gen += 1
         self._check(lib().qbe_collide_rk2(self._h, float(dt)), "qbe_collide_rk2")
 
     def step(self, dt, nsteps=1):
+        self._gen += 1
         self._check(lib().qbe_step(self._h, float(dt), int(nsteps)), "qbe_step")
+
+    # -- differentiation ---------------------------------------------------
+    def _like(self, x, shape, out):
+        if out is not None:
+            return out
+        if isinstance(x, np.ndarray):
+            return np.empty(shape)
+        import torch
+        return torch.empty(shape, dtype=torch.float64, device=x.device)
+
+    def collide_vjp(self, w, lam, out=None):
+        """(dC/dW at w)^T lam, cell by cell; w, lam, out of shape [ncells][4][N][N], same memory kind."""
+        ncells = w.shape[0]
+        shape = (ncells, 4, self.N, self.N)
+        pw, dev, k1 = _arg(w, shape)
+        pl, dev2, k2 = _arg(lam, shape)
+        out = self._like(w, shape, out)
+        po, dev3, k3 = _arg(out, shape)
+        if not (dev == dev2 == dev3):
+            raise ValueError("w, lam and out must all be host or all be device memory")
+        self._check(lib().qbe_collide_vjp(self._h, _c_void_p(pw), _c_void_p(pl), _c_void_p(po), ncells, dev),
+                    "qbe_collide_vjp")
+        return out
+
+    def step_checkpointed(self, dt, nsteps, checkpoint_every=20):
+        """step(dt, nsteps) recording the tape that step_vjp sweeps backwards."""
+        self._gen += 1
+        self._check(lib().qbe_step_checkpointed(self._h, float(dt), int(nsteps), int(checkpoint_every)),
+                    "qbe_step_checkpointed")
+        return self._gen
+
+    def step_vjp(self, lam_final, out=None, grad_B=None):
+        """(lam_init, grad_B) for the tape of the last step_checkpointed call."""
+        pl, dev, k1 = _arg(lam_final, self.state_shape)
+        out = self._like(lam_final, self.state_shape, out)
+        grad_B = self._like(lam_final, (self.Nx, 3), grad_B)
+        po, dev2, k2 = _arg(out, self.state_shape)
+        pb, dev3, k3 = _arg(grad_B, (self.Nx, 3))
+        if not (dev == dev2 == dev3):
+            raise ValueError("cotangents must all be host or all be device memory")
+        self._check(lib().qbe_step_vjp(self._h, _c_void_p(pl), _c_void_p(po), _c_void_p(pb), dev), "qbe_step_vjp")
+        return out, grad_B
+
+    def observables(self, w=None, out=None):
+        """[P_z, Phi_E] of w (default: the solver state)."""
+        if w is None:
+            out = np.empty(2) if out is None else out
+            po, dev, k = _arg(out, (2,))
+            self._check(lib().qbe_observables(self._h, None, _c_void_p(po), dev), "qbe_observables")
+            return out
+        pw, dev, k1 = _arg(w, self.state_shape)
+        out = self._like(w, (2,), out)
+        po, dev2, k2 = _arg(out, (2,))
+        if dev != dev2:
+            raise ValueError("w and out must both be host or both be device memory")
+        self._check(lib().qbe_observables(self._h, _c_void_p(pw), _c_void_p(po), dev), "qbe_observables")
+        return out
+
+    def observables_vjp(self, gbar, out=None):
+        """gbar[0] dP_z/dW + gbar[1] dPhi_E/dW."""
+        pg, dev, k1 = _arg(gbar, (2,))
+        out = self._like(gbar, self.state_shape, out)
+        po, dev2, k2 = _arg(out, self.state_shape)
+        if dev != dev2:
+            raise ValueError("gbar and out must both be host or both be device memory")
+        self._check(lib().qbe_observables_vjp(self._h, _c_void_p(pg), _c_void_p(po), dev), "qbe_observables_vjp")
+        return out
 
     def moments(self):
         rho = np.empty((self.Nx, 4))
