@@ -191,6 +191,55 @@ int qbe_observables(qbe_handle* h, const double* w, double* out, int on_device);
 /* lam = gbar[0] dP_z/dW + gbar[1] dPhi_E/dW ([Nx][4][N][N]); gbar[2]. */
 int qbe_observables_vjp(qbe_handle* h, const double* gbar, double* lam, int on_device);
 
+/* ---- Diagnostics (Sec. 2, Sec. 5) --------------------------------------
+ * A Fermi-Dirac state with mean velocity u (eq. W_FermiDirac; the average
+ * velocity shifts W_FD(v) -> W_FD(v - u), Sec. 5.2):
+ *   W_FD(v) = sum_s (exp((|v - u|^2/2 - mu_s)/T) + 1)^-1 |s><s|,
+ * T = k_B T, |up> = column 0 of U, |up><up| = (1 + bloch.sigma)/2. */
+typedef struct qbe_fermi_dirac {
+  double T;            /* k_B T; 0 when ok == 0 */
+  double mu_up;
+  double mu_dn;
+  double bloch[3];     /* unit Bloch vector of |up> */
+  double U_re[2][2];   /* U[row][col] = U_re + i U_im; columns |up>, |down> */
+  double U_im[2][2];
+  double u[2];         /* mean velocity */
+  int ok;              /* 1: fitted; 0: no Fermi-Dirac state has these moments */
+} qbe_fermi_dirac;
+
+/* Local entropy per cell S[W](x_j) = -int tr[W log W + (1 - W) log(1 - W)] dv
+ * (eq. entropy_def) as dv^2 sum_v over the eigenvalues w0 +- |w| (0 log 0 =
+ * 0): S[Nx]. */
+int qbe_entropy(qbe_handle* h, double* S, int on_device);
+
+/* Fermi-Dirac state with the moments (grid sums, eqs. density, velocity,
+ * internal_energy) of each cell (global = 0: out[Nx]) or of the whole domain
+ * (global = 1: x-averaged moments, out[1]).  The eigenbasis is that of the spin
+ * density rho (up = larger eigenvalue); T, mu_up, mu_dn solve eq.
+ * momentsFermiDirac for the eigenvalues of rho and the internal energy per
+ * particle (Sec. 5.2).  out is host memory.  A state whose internal energy
+ * is at or below the T -> 0 limit sum_s rho_s^2 / (4 pi tr rho), or with a
+ * non-positive eigenvalue of rho, gets ok = 0. */
+int qbe_fd_fit(qbe_handle* h, int global, qbe_fermi_dirac* out);
+
+/* The same fit for given moments (host only, no GPU): rho4 = Pauli components
+ * of int W dv, mom = int v tr W dv, energy = int |v|^2/2 tr W dv. */
+int qbe_fd_fit_moments(const double* rho4, const double* mom, double energy, qbe_fermi_dirac* out);
+
+/* Dilogarithm Li2(x) for real x <= 0 (host; the fit's special function):
+ * 't Hooft-Veltman Bernoulli series in -log(1 - x) on [-1, 0], inversion
+ * below -1.  NaN for x > 0. */
+double qbe_dilog(double x);
+
+/* Per cell: quantum relative entropy S(W(x_j) || F_j) = int tr[W (log W -
+ * log F) + (1 - W)(log(1 - W) - log(1 - F))] dv (eq. relentropy_hom) and, if
+ * l1 is not NULL, the distance int ||W - F||_1 dv (trace norm), with F_j =
+ * ref[j] (nref = Nx, local: eq. relentropy_local) or ref[0] (nref = 1, global:
+ * eq. relentropy_inhom); the x-integrals are the means over cells.  ref is host
+ * memory; rel[Nx], l1[Nx] host or device.  Errors: QBE_ERR_ARG (nref not 1 or
+ * Nx, a reference with ok == 0). */
+int qbe_relative_entropy(qbe_handle* h, const qbe_fermi_dirac* ref, int nref, double* rel, double* l1, int on_device);
+
 /* Number of kernel launches issued by the library since create (for
  * benchmarking bookkeeping). */
 long long qbe_launch_count(const qbe_handle* h);

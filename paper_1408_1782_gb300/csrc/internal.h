@@ -206,6 +206,20 @@ cudaError_t observables_launch(const double* W, int Nx, int N, double L, double*
                                cudaStream_t s, long long& launches);
 cudaError_t observables_vjp_launch(const double* gbar, int Nx, int N, double L, double* lam, cudaStream_t s,
                                    long long& launches);
+// Diagnostics (diagnostics.cu).  FdDev: one Fermi-Dirac state W_FD(v - u) with
+// the unit Bloch vector of its up state.
+struct FdDev {
+  double T, mu_up, mu_dn;
+  double bloch[3];
+  double u[2];
+};
+cudaError_t entropy_launch(const double* W, int Nx, int N, double L, double* out, cudaStream_t s,
+                           long long& launches);
+cudaError_t relative_entropy_launch(const double* W, int Nx, int N, double L, const FdDev* fd, int nfd, double* rel,
+                                    double* l1, cudaStream_t s, long long& launches);
+void fd_fit_from_moments(const double rho4[4], const double mom[2], double energy, qbe_fermi_dirac& out);
+double dilog(double x);
+
 cudaError_t moments_launch(const double* W, int Nx, int N, double L, double* out7, cudaStream_t s,
                            long long& launches);
 

@@ -626,6 +626,86 @@ int qbe_observables_vjp(qbe_handle* h, const double* gbar, double* lam, int on_d
   return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "observables_vjp");
 }
 
+int qbe_entropy(qbe_handle* h, double* S, int on_device) {
+  if (!h) return QBE_ERR_ARG;
+  if (!S) return fail(h, QBE_ERR_ARG, "entropy: null output");
+  if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
+  DeviceGuard dg(h->g.device);
+  if (h->small.ensure(small_elems(h)) != cudaSuccess) return fail(h, QBE_ERR_ALLOC, "diagnostics scratch");
+  double* dst = on_device ? S : h->small.p + 6;
+  cudaError_t e = entropy_launch(h->W, h->g.Nx, h->g.N, h->g.L, dst, h->stream, h->launches);
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(S, dst, (size_t)h->g.Nx * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "entropy");
+}
+
+int qbe_fd_fit_moments(const double* rho4, const double* mom, double energy, qbe_fermi_dirac* out) {
+  if (!rho4 || !mom || !out || !std::isfinite(energy)) return QBE_ERR_ARG;
+  fd_fit_from_moments(rho4, mom, energy, *out);
+  return QBE_OK;
+}
+
+double qbe_dilog(double x) { return dilog(x); }
+
+int qbe_fd_fit(qbe_handle* h, int global, qbe_fermi_dirac* out) {
+  if (!h) return QBE_ERR_ARG;
+  if (!out) return fail(h, QBE_ERR_ARG, "fd_fit: null output");
+  if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
+  DeviceGuard dg(h->g.device);
+  const int Nx = h->g.Nx;
+  cudaError_t e = moments_launch(h->W, Nx, h->g.N, h->g.L, h->mom, h->stream, h->launches);
+  std::vector<double> m((size_t)Nx * 7);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m.data(), h->mom, m.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fd_fit moments");
+  if (global) {
+    double avg[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < Nx; ++j)
+      for (int k = 0; k < 7; ++k) avg[k] += m[(size_t)j * 7 + k];
+    for (int k = 0; k < 7; ++k) avg[k] /= Nx;
+    fd_fit_from_moments(avg, avg + 4, avg[6], out[0]);
+    return QBE_OK;
+  }
+  for (int j = 0; j < Nx; ++j) fd_fit_from_moments(&m[(size_t)j * 7], &m[(size_t)j * 7 + 4], m[(size_t)j * 7 + 6], out[j]);
+  return QBE_OK;
+}
+
+int qbe_relative_entropy(qbe_handle* h, const qbe_fermi_dirac* ref, int nref, double* rel, double* l1, int on_device) {
+  if (!h) return QBE_ERR_ARG;
+  const int Nx = h->g.Nx;
+  if (!ref || !rel || (nref != 1 && nref != Nx)) return fail(h, QBE_ERR_ARG, "relative_entropy: bad arguments");
+  if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
+  std::vector<FdDev> fd((size_t)nref);
+  for (int k = 0; k < nref; ++k) {
+    if (!ref[k].ok || !(ref[k].T > 0.0)) return fail(h, QBE_ERR_ARG, "relative_entropy: reference not fitted");
+    fd[k].T = ref[k].T;
+    fd[k].mu_up = ref[k].mu_up;
+    fd[k].mu_dn = ref[k].mu_dn;
+    for (int c = 0; c < 3; ++c) fd[k].bloch[c] = ref[k].bloch[c];
+    fd[k].u[0] = ref[k].u[0];
+    fd[k].u[1] = ref[k].u[1];
+  }
+  DeviceGuard dg(h->g.device);
+  const size_t fd_doubles = (size_t)nref * sizeof(FdDev) / sizeof(double);
+  if (h->adj.ensure(5 * state_elems(h)) != cudaSuccess || h->small.ensure(small_elems(h)) != cudaSuccess)
+    return fail(h, QBE_ERR_ALLOC, "diagnostics scratch");
+  // reference states and (host path) outputs staged in the adjoint scratch, which is idle here
+  FdDev* dfd = reinterpret_cast<FdDev*>(h->adj.p);
+  double* drel = on_device ? rel : h->adj.p + fd_doubles;
+  double* dl1 = l1 ? (on_device ? l1 : h->adj.p + fd_doubles + Nx) : nullptr;
+  cudaError_t e = cudaMemcpyAsync(dfd, fd.data(), fd.size() * sizeof(FdDev), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = relative_entropy_launch(h->W, Nx, h->g.N, h->g.L, dfd, nref, drel, dl1, h->stream, h->launches);
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(rel, drel, (size_t)Nx * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && !on_device && l1)
+    e = cudaMemcpyAsync(l1, dl1, (size_t)Nx * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "relative_entropy");
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -34,6 +34,15 @@ class QbeFD(ctypes.Structure):
                 ("U_re", (_c_double * 2) * 2), ("U_im", (_c_double * 2) * 2)]
 
 
+class QbeFermiDirac(ctypes.Structure):
+    """Mirror of qbe_fermi_dirac (include/qbe.h)."""
+    _fields_ = [("T", _c_double), ("mu_up", _c_double), ("mu_dn", _c_double), ("bloch", _c_double * 3),
+                ("U_re", (_c_double * 2) * 2), ("U_im", (_c_double * 2) * 2), ("u", _c_double * 2), ("ok", _c_int)]
+
+    def U(self):
+        return np.array([[complex(self.U_re[r][c], self.U_im[r][c]) for c in range(2)] for r in range(2)])
+
+
 SIGNATURES = {
     "qbe_create": (_c_int, [ctypes.POINTER(QbeGrid), ctypes.POINTER(_c_void_p)]),
     "qbe_destroy": (None, [_c_void_p]),
@@ -56,6 +65,11 @@ SIGNATURES = {
     "qbe_step_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_observables": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_observables_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int]),
+    "qbe_entropy": (_c_int, [_c_void_p, _c_void_p, _c_int]),
+    "qbe_fd_fit": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "qbe_fd_fit_moments": (_c_int, [_c_void_p, _c_void_p, _c_double, _c_void_p]),
+    "qbe_dilog": (_c_double, [_c_double]),
+    "qbe_relative_entropy": (_c_int, [_c_void_p, _c_void_p, _c_int, _c_void_p, _c_void_p, _c_int]),
     "qbe_collide_noalloc": (_c_int, [ctypes.POINTER(QbeGrid), _c_void_p, _c_void_p, _c_int, _c_void_p]),
     "qbe_batch_create": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, ctypes.POINTER(_c_void_p)]),
     "qbe_batch_destroy": (None, [_c_void_p]),
@@ -352,6 +366,32 @@ class Solver:
         self._check(lib().qbe_observables_vjp(self._h, _c_void_p(pg), _c_void_p(po), dev), "qbe_observables_vjp")
         return out
 
+    # -- diagnostics (Sec. 2, Sec. 5) ----------------------------------------
+    def entropy(self):
+        """Local entropy per cell, [Nx] (host)."""
+        out = np.empty(self.Nx)
+        self._check(lib().qbe_entropy(self._h, _c_void_p(out.ctypes.data), 0), "qbe_entropy")
+        return out
+
+    def fd_fit(self, global_fit=False):
+        """Fermi-Dirac states with the moments of each cell (list of Nx QbeFermiDirac) or of the domain (one)."""
+        n = 1 if global_fit else self.Nx
+        arr = (QbeFermiDirac * n)()
+        self._check(lib().qbe_fd_fit(self._h, 1 if global_fit else 0, ctypes.cast(arr, _c_void_p)), "qbe_fd_fit")
+        return arr[0] if global_fit else list(arr)
+
+    def relative_entropy(self, ref, with_l1=True):
+        """(rel[Nx], l1[Nx] or None) to ref: one QbeFermiDirac (global) or a list of Nx (local)."""
+        refs = [ref] if isinstance(ref, QbeFermiDirac) else list(ref)
+        arr = (QbeFermiDirac * len(refs))(*refs)
+        rel = np.empty(self.Nx)
+        l1 = np.empty(self.Nx) if with_l1 else None
+        self._check(lib().qbe_relative_entropy(self._h, ctypes.cast(arr, _c_void_p), len(refs),
+                                               _c_void_p(rel.ctypes.data),
+                                               _c_void_p(l1.ctypes.data) if with_l1 else None, 0),
+                    "qbe_relative_entropy")
+        return rel, l1
+
     def moments(self):
         rho = np.empty((self.Nx, 4))
         mom = np.empty((self.Nx, 2))
@@ -372,3 +412,20 @@ class Solver:
         self._check(lib().qbe_kernel_time(self._h, KERNEL_GROUPS[group], ctypes.byref(ms), ctypes.byref(n)),
                     "qbe_kernel_time")
         return ms.value, n.value
+
+
+def fd_fit_moments(rho4, mom, energy) -> QbeFermiDirac:
+    """Fermi-Dirac fit for given moments (host only; no GPU needed)."""
+    r = np.ascontiguousarray(rho4, dtype=np.float64)
+    m = np.ascontiguousarray(mom, dtype=np.float64)
+    out = QbeFermiDirac()
+    rc = lib().qbe_fd_fit_moments(_c_void_p(r.ctypes.data), _c_void_p(m.ctypes.data), float(energy),
+                                  ctypes.cast(ctypes.byref(out), _c_void_p))
+    if rc != 0:
+        raise QbeError(f"qbe_fd_fit_moments failed with code {rc}")
+    return out
+
+
+def dilog(x: float) -> float:
+    """Li2(x), x <= 0 (the library's own implementation)."""
+    return float(lib().qbe_dilog(float(x)))
