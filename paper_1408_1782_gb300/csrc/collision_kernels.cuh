@@ -34,6 +34,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "fft.cuh"
 #include "internal.h"
@@ -325,6 +326,99 @@ __global__ void __launch_bounds__(kThreads, 3) k_i3(const typename Vec2Of<T>::ty
 }
 
 // --------------------------------------------------------------------------
+// I3 with the transform field resident in shared memory (FP32, n <= 128: an
+// n x (n+1) complex float field is at most 129 KB).  Same units, arithmetic
+// and accumulation order as k_i3 (the line transforms are the same code, so
+// results are bitwise identical); each convolution (row FFT, column psi'
+// convolution, row IFFT) runs entirely on chip, global memory holds only the
+// two shifted fields per block and the partial sums.
+// --------------------------------------------------------------------------
+constexpr int kThreadsI3Smem = 512;
+
+template <int n>
+__global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const float2* what, const float2* wfine, float2* K3part,
+                                                             float2* ws, const float2* __restrict__ gtw,
+                                                             const float* __restrict__ psip_s,
+                                                             const float2* __restrict__ phase, int J, int M, int nmc,
+                                                             int mch, int nunits) {
+  using C2 = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* G = tw + n;                       // [n][LS]
+  constexpr int LS = n + 1, P = n * n;
+  __shared__ unsigned char xmask[n];
+  for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
+    const int k = freq_of_pos<n>(pos);
+    xmask[pos] = ((k < n / 4) || (k >= n - n / 4)) ? 1 : 0;
+  }
+  load_twiddles<n>(tw, gtw);
+  C2* Sig = ws + (size_t)blockIdx.x * 3 * P;   // [2][P]
+  for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    const int c = unit / (J * nmc);
+    const int j = (unit / nmc) % J;
+    const int mc = unit % nmc;
+    C2* acc = K3part + (size_t)unit * 2 * P;
+    zero_fields(acc, 2 * P);
+    const float* psp = psip_s + (size_t)j * P;
+    const C2* wf = wfine + (size_t)c * 2 * P;
+    const int m0 = mc * mch, m1 = min(M, m0 + mch);
+    for (int m = m0; m < m1; ++m) {
+      const C2* px = phase + ((size_t)j * M + m) * 2 * n;
+      const C2* py = px + n;
+      for (int p = 0; p < 2; ++p) {
+        const C2* in = what + ((size_t)c * 4 + p) * P;
+        for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+          const int ix = idx / n, iy = idx % n;
+          G[ix * LS + iy] = (xmask[ix] && xmask[iy]) ? cmul(in[idx], cmul(px[ix], py[iy])) : zero2<float>();
+        }
+        __syncthreads();
+        fft_lines<n, 1>(G, n, 1, LS, tw);     // columns (along ix)
+        fft_lines<n, 1>(G, n, LS, 1, tw);     // rows (along iy)
+        C2* S = Sig + (size_t)p * P;
+        for (int idx = threadIdx.x; idx < P; idx += blockDim.x) S[idx] = G[(idx / n) * LS + idx % n];
+        __syncthreads();
+      }
+      for (int a = 0; a < 4; ++a) {
+        const C2* wa = wf + (size_t)(a >> 1) * P;
+        const C2* Sa = Sig + (size_t)(a >> 1) * P;
+        const bool im = (a & 1) != 0;
+        const float eta = (a == 0) ? 1.f : -1.f;
+        for (int p = 0; p < 2; ++p) {
+          const C2* Sp = Sig + (size_t)p * P;
+          C2* accp = acc + (size_t)p * P;
+          for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+            const C2 z = wa[idx];
+            G[(idx / n) * LS + idx % n] = cscale(Sp[idx], im ? z.y : z.x);
+          }
+          __syncthreads();
+          fft_lines<n, -1>(G, n, LS, 1, tw);                                           // rows forward
+          fft_conv_lines<n>(G, n, 1, LS, tw, [&](int l, int pos) { return psp[pos * n + l]; });   // columns
+          fft_lines<n, 1>(G, n, LS, 1, tw);                                            // rows inverse
+          for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+            const C2 v = G[(idx / n) * LS + idx % n];
+            const C2 s2 = Sa[idx];
+            const float f = eta * (im ? s2.y : s2.x);
+            const C2 d = accp[idx];
+            accp[idx] = mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y));
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+}
+
+template <int n>
+constexpr bool use_i3_smem() {
+  return n <= 128;
+}
+
+template <int n>
+constexpr size_t i3_smem_bytes() {
+  return (size_t)(n + n * (n + 1)) * sizeof(float2);
+}
+
+// --------------------------------------------------------------------------
 // Assemble C on the fine grid from D, K2, K3, K4 (Pauli formulas of Sec. 3.1),
 // then FFT, cut to Xi (without the -N/2 line), inverse FFT and sample the
 // coarse nodes.  One block per cell.  The K3 partial sums are added in FP64.
@@ -428,6 +522,8 @@ void set_smem_attributes() {
   cudaFuncSetAttribute(k_i24<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i3<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_assemble<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+    cudaFuncSetAttribute(k_i3_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
   done = true;
 }
 
@@ -435,7 +531,10 @@ template <int n, class T>
 int i3_blocks_per_sm() {
   set_smem_attributes<n, T>();
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n, T>, kThreads, smem_bytes<n, T>());
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>());
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n, T>, kThreads, smem_bytes<n, T>());
   return b < 1 ? 1 : b;
 }
 
@@ -467,8 +566,12 @@ cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w,
   const int nunits = ncells * t.J * cw.nmc;
   const int grid = nunits < cw.grid_i3 ? nunits : cw.grid_i3;
   begin(KG_I3);
-  k_i3<n, T><<<grid, kThreads, sm, s>>>(what, wfine, K3part, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M, cw.nmc,
-                                        cw.mch, nunits);
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+    k_i3_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(what, wfine, K3part, ws, tb.tw, tb.psip_s, tb.phase,
+                                                                  t.J, t.M, cw.nmc, cw.mch, nunits);
+  else
+    k_i3<n, T><<<grid, kThreads, sm, s>>>(what, wfine, K3part, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M, cw.nmc,
+                                          cw.mch, nunits);
   end();
   begin(KG_ASSEMBLE);
   k_assemble<n, T><<<ncells, kThreads, sm, s>>>(wfine, Dacc, K2acc, K4acc, K3part, t.J * cw.nmc, ws, tb.tw, c);

@@ -469,6 +469,133 @@ __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
 }
 
 // --------------------------------------------------------------------------
+// I3 transpose with the transform field resident in shared memory (FP32,
+// n <= 128), the counterpart of k_i3_smem.  Each convolution's epilogue adds
+// its terms straight into the accumulators, so T_ab and Q_ab are never stored:
+//   after T_ap = Psi'(w_a S_p):  XZ_a += eta_a mu_p . T_ap           (i)
+//   after Q_ap = Psi'(S_a mu_p): part_r_a += eta_a Q_ap . S_p         (ii)
+//                                XZ_p += eta_a w_a Q_ap               (iii)
+// then S^T of XZ in Fourier space as in k_i3_vjp.
+// --------------------------------------------------------------------------
+template <int n>
+__global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
+    const float2* what, const float2* wfine, const float2* mu3, float2* part_r, float2* part_s, float2* ws,
+    const float2* __restrict__ gtw, const float* __restrict__ psip_s, const float2* __restrict__ phase, int J, int M,
+    int nmc, int mch, int nunits) {
+  using C2 = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* G = tw + n;
+  constexpr int LS = n + 1, P = n * n;
+  __shared__ unsigned char xmask[n];
+  for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
+    const int k = freq_of_pos<n>(pos);
+    xmask[pos] = ((k < n / 4) || (k >= n - n / 4)) ? 1 : 0;
+  }
+  load_twiddles<n>(tw, gtw);
+  C2* slot = ws + (size_t)blockIdx.x * 9 * P;
+  C2* Sig = slot;            // [2]
+  C2* XZ = slot + 2 * P;     // [2]
+  for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    const int c = unit / (J * nmc);
+    const int j = (unit / nmc) % J;
+    const int mc = unit % nmc;
+    C2* accr = part_r + (size_t)unit * 2 * P;
+    C2* accs = part_s + (size_t)unit * 2 * P;
+    zero_fields(accr, 2 * P);
+    zero_fields(accs, 2 * P);
+    const float* psp = psip_s + (size_t)j * P;
+    const C2* wf = wfine + (size_t)c * 2 * P;
+    const C2* mu = mu3 + (size_t)c * 2 * P;
+    const int m0 = mc * mch, m1 = min(M, m0 + mch);
+    for (int m = m0; m < m1; ++m) {
+      const C2* px = phase + ((size_t)j * M + m) * 2 * n;
+      const C2* py = px + n;
+      for (int p = 0; p < 2; ++p) {
+        const C2* in = what + ((size_t)c * 4 + p) * P;
+        for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+          const int ix = idx / n, iy = idx % n;
+          G[ix * LS + iy] = (xmask[ix] && xmask[iy]) ? cmul(in[idx], cmul(px[ix], py[iy])) : zero2<float>();
+        }
+        __syncthreads();
+        fft_lines<n, 1>(G, n, 1, LS, tw);
+        fft_lines<n, 1>(G, n, LS, 1, tw);
+        C2* S = Sig + (size_t)p * P;
+        for (int idx = threadIdx.x; idx < P; idx += blockDim.x) S[idx] = G[(idx / n) * LS + idx % n];
+        __syncthreads();
+      }
+      zero_fields(XZ, 2 * P);
+      for (int a = 0; a < 4; ++a) {
+        const C2* wa = wf + (size_t)(a >> 1) * P;
+        const C2* Sa = Sig + (size_t)(a >> 1) * P;
+        C2* XZa = XZ + (size_t)(a >> 1) * P;
+        C2* accra = accr + (size_t)(a >> 1) * P;
+        const bool im = (a & 1) != 0;
+        const float eta_a = (a == 0) ? 1.f : -1.f;
+        for (int p = 0; p < 2; ++p) {
+          const C2* Sp = Sig + (size_t)p * P;
+          const C2* mup = mu + (size_t)p * P;
+          C2* XZp = XZ + (size_t)p * P;
+          for (int which = 0; which < 2; ++which) {
+            for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+              C2 v;
+              if (which == 0) {
+                const C2 z = wa[idx];
+                v = cscale(Sp[idx], im ? z.y : z.x);
+              } else {
+                const C2 s2 = Sa[idx];
+                v = cscale(mup[idx], im ? s2.y : s2.x);
+              }
+              G[(idx / n) * LS + idx % n] = v;
+            }
+            __syncthreads();
+            fft_lines<n, -1>(G, n, LS, 1, tw);
+            fft_conv_lines<n>(G, n, 1, LS, tw, [&](int l, int pos) { return psp[pos * n + l]; });
+            fft_lines<n, 1>(G, n, LS, 1, tw);
+            for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+              const C2 g = G[(idx / n) * LS + idx % n];
+              if (which == 0) {
+                const C2 mv = mup[idx];
+                const float x = eta_a * (mv.x * g.x + mv.y * g.y);
+                if (im) XZa[idx].y += x; else XZa[idx].x += x;
+              } else {
+                const C2 sp = Sp[idx];
+                const float y = eta_a * (g.x * sp.x + g.y * sp.y);
+                if (im) accra[idx].y += y; else accra[idx].x += y;
+                const C2 z = wa[idx];
+                const float e = eta_a * (im ? z.y : z.x);
+                C2 o = XZp[idx];
+                o.x += e * g.x;
+                o.y += e * g.y;
+                XZp[idx] = o;
+              }
+            }
+            __syncthreads();
+          }
+        }
+      }
+      for (int p = 0; p < 2; ++p) {
+        const C2* src = XZ + (size_t)p * P;
+        C2* dst = accs + (size_t)p * P;
+        for (int idx = threadIdx.x; idx < P; idx += blockDim.x) G[(idx / n) * LS + idx % n] = src[idx];
+        __syncthreads();
+        fft_lines<n, -1>(G, n, LS, 1, tw);    // rows
+        fft_lines<n, -1>(G, n, 1, LS, tw);    // columns
+        for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+          const int ix = idx / n, iy = idx % n;
+          const C2 z = cmulc(G[ix * LS + iy], cmul(px[ix], py[iy]));
+          C2 d = dst[idx];
+          d.x += z.x;
+          d.y += z.y;
+          dst[idx] = d;
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
 // Final: nu = direct + I1 + I2/I4 + 2 nu_f (into w0) + sum of the I3 real
 // partials + IFFT(sum of the I3 spectral partials / n^2); gradient = 4 E P nu.
 // One block per cell; writes grad[c][4][N][N] (FP64).
@@ -557,6 +684,8 @@ void set_vjp_smem_attributes() {
   cudaFuncSetAttribute(k_i24_vjp<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i3_vjp<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_vjp_final<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+    cudaFuncSetAttribute(k_i3_vjp_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
   done = true;
 }
 
@@ -596,8 +725,13 @@ cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const
   const int nunits = ncells * t.J * vw.nmc;
   const int grid = nunits < vw.grid ? nunits : vw.grid;
   begin(KG_VJP_I3);
-  k_i3_vjp<n, T><<<grid, kThreads, sm, s>>>(what, wfine, mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw, tb.psip_s,
-                                            tb.phase, t.J, t.M, vw.nmc, vw.mch, nunits);
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+    k_i3_vjp_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(what, wfine, mu3, (C2*)vw.part_r,
+                                                                      (C2*)vw.part_s, ws, tb.tw, tb.psip_s, tb.phase,
+                                                                      t.J, t.M, vw.nmc, vw.mch, nunits);
+  else
+    k_i3_vjp<n, T><<<grid, kThreads, sm, s>>>(what, wfine, mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw,
+                                              tb.psip_s, tb.phase, t.J, t.M, vw.nmc, vw.mch, nunits);
   end();
   begin(KG_VJP);
   k_vjp_final<n, T><<<ncells, kThreads, sm, s>>>(nu, nuf, (C2*)vw.part_r, (C2*)vw.part_s, t.J * vw.nmc, ws, tb.tw,
@@ -611,7 +745,10 @@ template <int n, class T>
 int i3_vjp_blocks_per_sm() {
   set_vjp_smem_attributes<n, T>();
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_vjp<n, T>, kThreads, smem_bytes<n, T>());
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_vjp_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>());
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_vjp<n, T>, kThreads, smem_bytes<n, T>());
   return b < 1 ? 1 : b;
 }
 

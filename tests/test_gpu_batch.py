@@ -57,11 +57,14 @@ def test_batch_graph_steps_match_individual_steps(qbe, tune):
         for s, W, _ in batch_sims:
             s.set_state(W)                      # autotuning evaluated C[W] only; reset anyway
     b.step(dt, 3)
-    for (s, W, B), (s1, _, _) in zip(batch_sims, solo):
+    for (s, W, B), (s1, _, _), case in zip(batch_sims, solo, CASES):
         s1.step(dt, 3)
         got, ref = s.get_state(), s1.get_state()
         if tune:
-            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+            # a tuned m-chunking regroups the per-unit partial sums of I3: FP64 rounding in the plain form,
+            # FP32 rounding in the FP32-split form
+            tol = 1e-12 if case[3] == 0 else 1e-6
+            assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
         else:
             assert np.array_equal(got, ref)
     b.close()
