@@ -345,7 +345,9 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const float2* wha
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
   C2* G = tw + n;                       // [n][LS]
+  float* psm = reinterpret_cast<float*>(G + n * (n + 1));   // psi'_j of the current unit, [n][n]
   constexpr int LS = n + 1, P = n * n;
+  constexpr int kIter = (P + kThreadsI3Smem - 1) / kThreadsI3Smem;
   __shared__ unsigned char xmask[n];
   for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
     const int k = freq_of_pos<n>(pos);
@@ -359,7 +361,12 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const float2* wha
     const int mc = unit % nmc;
     C2* acc = K3part + (size_t)unit * 2 * P;
     zero_fields(acc, 2 * P);
-    const float* psp = psip_s + (size_t)j * P;
+    {
+      const float4* src = reinterpret_cast<const float4*>(psip_s + (size_t)j * P);
+      float4* dst = reinterpret_cast<float4*>(psm);
+      for (int i4 = threadIdx.x; i4 < P / 4; i4 += blockDim.x) dst[i4] = src[i4];
+      __syncthreads();
+    }
     const C2* wf = wfine + (size_t)c * 2 * P;
     const int m0 = mc * mch, m1 = min(M, m0 + mch);
     for (int m = m0; m < m1; ++m) {
@@ -384,22 +391,34 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const float2* wha
         const bool im = (a & 1) != 0;
         const float eta = (a == 0) ? 1.f : -1.f;
         for (int p = 0; p < 2; ++p) {
-          const C2* Sp = Sig + (size_t)p * P;
-          C2* accp = acc + (size_t)p * P;
-          for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
-            const C2 z = wa[idx];
-            G[(idx / n) * LS + idx % n] = cscale(Sp[idx], im ? z.y : z.x);
+          const C2* __restrict__ Sp = Sig + (size_t)p * P;
+          const C2* __restrict__ wv = wa;
+          const C2* __restrict__ sa = Sa;
+          C2* __restrict__ accp = acc + (size_t)p * P;
+          // element loops with a compile-time trip count, unrolled so each thread keeps several
+          // L2 loads in flight (one block per SM leaves few warps to hide their latency)
+#pragma unroll 8
+          for (int k = 0; k < kIter; ++k) {
+            const int idx = threadIdx.x + k * kThreadsI3Smem;
+            if (kIter * kThreadsI3Smem == P || idx < P) {
+              const C2 z = wv[idx];
+              G[(idx / n) * LS + idx % n] = cscale(Sp[idx], im ? z.y : z.x);
+            }
           }
           __syncthreads();
           fft_lines<n, -1>(G, n, LS, 1, tw);                                           // rows forward
-          fft_conv_lines<n>(G, n, 1, LS, tw, [&](int l, int pos) { return psp[pos * n + l]; });   // columns
+          fft_conv_lines<n>(G, n, 1, LS, tw, [&](int l, int pos) { return psm[pos * n + l]; });   // columns
           fft_lines<n, 1>(G, n, LS, 1, tw);                                            // rows inverse
-          for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
-            const C2 v = G[(idx / n) * LS + idx % n];
-            const C2 s2 = Sa[idx];
-            const float f = eta * (im ? s2.y : s2.x);
-            const C2 d = accp[idx];
-            accp[idx] = mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y));
+#pragma unroll 8
+          for (int k = 0; k < kIter; ++k) {
+            const int idx = threadIdx.x + k * kThreadsI3Smem;
+            if (kIter * kThreadsI3Smem == P || idx < P) {
+              const C2 v = G[(idx / n) * LS + idx % n];
+              const C2 s2 = sa[idx];
+              const float f = eta * (im ? s2.y : s2.x);
+              const C2 d = accp[idx];
+              accp[idx] = mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y));
+            }
           }
           __syncthreads();
         }
@@ -414,8 +433,8 @@ constexpr bool use_i3_smem() {
 }
 
 template <int n>
-constexpr size_t i3_smem_bytes() {
-  return (size_t)(n + n * (n + 1)) * sizeof(float2);
+constexpr size_t i3_smem_bytes() {   // twiddles, the field (padded rows), psi'_j
+  return (size_t)(n + n * (n + 1)) * sizeof(float2) + (size_t)n * n * sizeof(float);
 }
 
 // --------------------------------------------------------------------------

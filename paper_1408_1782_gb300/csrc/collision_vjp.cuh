@@ -485,8 +485,10 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
   using C2 = float2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
-  C2* G = tw + n;
+  C2* G = tw + n;                       // [n][LS]
+  float* psm = reinterpret_cast<float*>(G + n * (n + 1));   // psi'_j of the current unit, [n][n]
   constexpr int LS = n + 1, P = n * n;
+  constexpr int kIter = (P + kThreadsI3Smem - 1) / kThreadsI3Smem;
   __shared__ unsigned char xmask[n];
   for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
     const int k = freq_of_pos<n>(pos);
@@ -504,7 +506,12 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
     C2* accs = part_s + (size_t)unit * 2 * P;
     zero_fields(accr, 2 * P);
     zero_fields(accs, 2 * P);
-    const float* psp = psip_s + (size_t)j * P;
+    {
+      const float4* src = reinterpret_cast<const float4*>(psip_s + (size_t)j * P);
+      float4* dst = reinterpret_cast<float4*>(psm);
+      for (int i4 = threadIdx.x; i4 < P / 4; i4 += blockDim.x) dst[i4] = src[i4];
+      __syncthreads();
+    }
     const C2* wf = wfine + (size_t)c * 2 * P;
     const C2* mu = mu3 + (size_t)c * 2 * P;
     const int m0 = mc * mch, m1 = min(M, m0 + mch);
@@ -537,37 +544,51 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
           const C2* mup = mu + (size_t)p * P;
           C2* XZp = XZ + (size_t)p * P;
           for (int which = 0; which < 2; ++which) {
-            for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
-              C2 v;
-              if (which == 0) {
-                const C2 z = wa[idx];
-                v = cscale(Sp[idx], im ? z.y : z.x);
-              } else {
-                const C2 s2 = Sa[idx];
-                v = cscale(mup[idx], im ? s2.y : s2.x);
+            const C2* __restrict__ src = which == 0 ? Sp : mup;
+            const C2* __restrict__ scl = which == 0 ? wa : Sa;
+#pragma unroll 8
+            for (int k = 0; k < kIter; ++k) {
+              const int idx = threadIdx.x + k * kThreadsI3Smem;
+              if (kIter * kThreadsI3Smem == P || idx < P) {
+                const C2 z = scl[idx];
+                G[(idx / n) * LS + idx % n] = cscale(src[idx], im ? z.y : z.x);
               }
-              G[(idx / n) * LS + idx % n] = v;
             }
             __syncthreads();
             fft_lines<n, -1>(G, n, LS, 1, tw);
-            fft_conv_lines<n>(G, n, 1, LS, tw, [&](int l, int pos) { return psp[pos * n + l]; });
+            fft_conv_lines<n>(G, n, 1, LS, tw, [&](int l, int pos) { return psm[pos * n + l]; });
             fft_lines<n, 1>(G, n, LS, 1, tw);
-            for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
-              const C2 g = G[(idx / n) * LS + idx % n];
-              if (which == 0) {
-                const C2 mv = mup[idx];
-                const float x = eta_a * (mv.x * g.x + mv.y * g.y);
-                if (im) XZa[idx].y += x; else XZa[idx].x += x;
-              } else {
-                const C2 sp = Sp[idx];
-                const float y = eta_a * (g.x * sp.x + g.y * sp.y);
-                if (im) accra[idx].y += y; else accra[idx].x += y;
-                const C2 z = wa[idx];
-                const float e = eta_a * (im ? z.y : z.x);
-                C2 o = XZp[idx];
-                o.x += e * g.x;
-                o.y += e * g.y;
-                XZp[idx] = o;
+            if (which == 0) {
+              const C2* __restrict__ mv_ = mup;
+              float* __restrict__ xz = reinterpret_cast<float*>(XZa) + (im ? 1 : 0);
+#pragma unroll 8
+              for (int k = 0; k < kIter; ++k) {
+                const int idx = threadIdx.x + k * kThreadsI3Smem;
+                if (kIter * kThreadsI3Smem == P || idx < P) {
+                  const C2 g = G[(idx / n) * LS + idx % n];
+                  const C2 mv = mv_[idx];
+                  xz[2 * idx] += eta_a * (mv.x * g.x + mv.y * g.y);
+                }
+              }
+            } else {
+              const C2* __restrict__ sp_ = Sp;
+              const C2* __restrict__ wa_ = wa;
+              float* __restrict__ ar = reinterpret_cast<float*>(accra) + (im ? 1 : 0);
+              C2* __restrict__ xzp = XZp;
+#pragma unroll 4
+              for (int k = 0; k < kIter; ++k) {
+                const int idx = threadIdx.x + k * kThreadsI3Smem;
+                if (kIter * kThreadsI3Smem == P || idx < P) {
+                  const C2 g = G[(idx / n) * LS + idx % n];
+                  const C2 sp = sp_[idx];
+                  const C2 z = wa_[idx];
+                  ar[2 * idx] += eta_a * (g.x * sp.x + g.y * sp.y);
+                  const float e = eta_a * (im ? z.y : z.x);
+                  C2 o = xzp[idx];
+                  o.x += e * g.x;
+                  o.y += e * g.y;
+                  xzp[idx] = o;
+                }
               }
             }
             __syncthreads();
