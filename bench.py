@@ -41,9 +41,10 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (profiles/fp64_fp32_issue_rates.md)
 FP32_FMA_PER_CLK_PER_SM = 128        # measured 116 FFMA/clk/SM
-# DRAM bytes (read + write) per (cell, j, m) unit of k_i3 from one ncu capture of an 8-cell slice
-# (profiles/k_i3_f64_n64_8cells.md, profiles/k_i3_f32_n64_8cells.md), N = 64 only; scaled by units.
-I3_DRAM_BYTES_PER_UNIT = {(64, 0): 122.37e9 / 8192, (64, 1): 49.61e9 / 8192}
+# DRAM bytes (read + write) per (cell, j, m) unit of the I3 kernel from one ncu capture of an 8-cell
+# slice of the current kernel (profiles/), scaled by units; absent when no capture of the current
+# kernel exists.
+I3_DRAM_BYTES_PER_UNIT = {}
 
 
 def workload(name="plain_fp64_n64", precision=None):

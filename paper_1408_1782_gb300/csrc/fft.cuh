@@ -347,6 +347,7 @@ __device__ __forceinline__ void row_pass(C2* sm, const C2* tw, LD ld, MID mid, S
   constexpr int RC = Chunk<n, sizeof(C2)>::RC, LS = Chunk<n, sizeof(C2)>::LS;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int r0 = 0; r0 < n; r0 += RC) {
+#pragma unroll 4
     for (int idx = tid; idx < RC * n; idx += nt) {
       const int r = idx / n, iy = idx % n;
       sm[r * LS + iy] = ld(r0 + r, iy);
@@ -354,13 +355,15 @@ __device__ __forceinline__ void row_pass(C2* sm, const C2* tw, LD ld, MID mid, S
     __syncthreads();
     if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1)>(sm, RC, LS, 1, tw);
     if (HAS_MID) {
-      for (int idx = tid; idx < RC * n; idx += nt) {
+  #pragma unroll 4
+    for (int idx = tid; idx < RC * n; idx += nt) {
         const int r = idx / n, iy = idx % n;
         sm[r * LS + iy] = mid(r0 + r, iy, sm[r * LS + iy]);
       }
       __syncthreads();
     }
     if (DIR2 != 0) fft_lines<n, (DIR2 < 0 ? -1 : 1)>(sm, RC, LS, 1, tw);
+#pragma unroll 4
     for (int idx = tid; idx < RC * n; idx += nt) {
       const int r = idx / n, iy = idx % n;
       st(r0 + r, iy, sm[r * LS + iy]);
@@ -375,6 +378,7 @@ __device__ __forceinline__ void col_pass(C2* sm, const C2* tw, LD ld, MID mid, S
   constexpr int CC = Chunk<n, sizeof(C2)>::CC;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < n; c0 += CC) {
+#pragma unroll 4
     for (int idx = tid; idx < CC * n; idx += nt) {
       const int ix = idx / CC, c = idx % CC;
       sm[ix * CC + c] = ld(ix, c0 + c);
@@ -382,13 +386,15 @@ __device__ __forceinline__ void col_pass(C2* sm, const C2* tw, LD ld, MID mid, S
     __syncthreads();
     if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1)>(sm, CC, 1, CC, tw);
     if (HAS_MID) {
-      for (int idx = tid; idx < CC * n; idx += nt) {
+  #pragma unroll 4
+    for (int idx = tid; idx < CC * n; idx += nt) {
         const int ix = idx / CC, c = idx % CC;
         sm[ix * CC + c] = mid(ix, c0 + c, sm[ix * CC + c]);
       }
       __syncthreads();
     }
     if (DIR2 != 0) fft_lines<n, (DIR2 < 0 ? -1 : 1)>(sm, CC, 1, CC, tw);
+#pragma unroll 4
     for (int idx = tid; idx < CC * n; idx += nt) {
       const int ix = idx / CC, c = idx % CC;
       st(ix, c0 + c, sm[ix * CC + c]);
@@ -404,12 +410,14 @@ __device__ __forceinline__ void col_conv_pass(C2* sm, const C2* tw, LD ld, MUL m
   constexpr int CC = Chunk<n, sizeof(C2)>::CC;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < n; c0 += CC) {
+#pragma unroll 4
     for (int idx = tid; idx < CC * n; idx += nt) {
       const int ix = idx / CC, c = idx % CC;
       sm[ix * CC + c] = ld(ix, c0 + c);
     }
     __syncthreads();
     fft_conv_lines<n>(sm, CC, 1, CC, tw, [&](int l, int pos) { return mul(pos, c0 + l); });
+#pragma unroll 4
     for (int idx = tid; idx < CC * n; idx += nt) {
       const int ix = idx / CC, c = idx % CC;
       st(ix, c0 + c, sm[ix * CC + c]);
@@ -426,6 +434,7 @@ __device__ __forceinline__ void col_pass_list(C2* sm, const C2* tw, const int* c
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < ncols; c0 += CC) {
     const int nc = (ncols - c0) < CC ? (ncols - c0) : CC;
+#pragma unroll 4
     for (int idx = tid; idx < nc * n; idx += nt) {
       const int ix = idx / nc, c = idx % nc;
       sm[ix * CC + c] = ld(ix, cols[c0 + c]);
@@ -433,13 +442,15 @@ __device__ __forceinline__ void col_pass_list(C2* sm, const C2* tw, const int* c
     __syncthreads();
     if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1)>(sm, nc, 1, CC, tw);
     if (HAS_MID) {
-      for (int idx = tid; idx < nc * n; idx += nt) {
+  #pragma unroll 4
+    for (int idx = tid; idx < nc * n; idx += nt) {
         const int ix = idx / nc, c = idx % nc;
         sm[ix * CC + c] = mid(ix, cols[c0 + c], sm[ix * CC + c]);
       }
       __syncthreads();
     }
     if (DIR2 != 0) fft_lines<n, (DIR2 < 0 ? -1 : 1)>(sm, nc, 1, CC, tw);
+#pragma unroll 4
     for (int idx = tid; idx < nc * n; idx += nt) {
       const int ix = idx / nc, c = idx % nc;
       st(ix, cols[c0 + c], sm[ix * CC + c]);
