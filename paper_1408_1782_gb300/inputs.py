@@ -220,3 +220,16 @@ def random_field(shape, seed: int = 0, scale: float = 1.0) -> np.ndarray:
     """Seeded standard-normal field of the given shape (tangent directions and cotangents)."""
     rng = np.random.default_rng(seed)
     return np.ascontiguousarray(scale * rng.standard_normal(shape))
+
+
+def fermi_dirac_w(N: int, Nx: int, beta: float, mu_up: float, mu_dn: float, U=None, L: float = 12.0) -> np.ndarray:
+    """Uniform Fermi-Dirac state (eq. W_FermiDirac) in every cell; U's columns are the spin basis; [Nx,4,N,N]."""
+    vx, vy = velocity_mesh(N, L)
+    e = 0.5 * (vx**2 + vy**2)
+    U = np.eye(2, dtype=np.complex128) if U is None else np.asarray(U, dtype=np.complex128)
+    D = np.zeros((N, N, 2, 2), dtype=np.complex128)
+    D[..., 0, 0] = _fd_occupation(beta, e, mu_up)
+    D[..., 1, 1] = _fd_occupation(beta, e, mu_dn)
+    Wm = U[None, None] @ D @ np.conj(U.T)[None, None]
+    w = np.moveaxis(matrix_to_pauli(Wm), -1, 0)
+    return np.ascontiguousarray(np.repeat(w[None], Nx, axis=0))
