@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_i3(const typename Vec2Of<T>::ty
 // convolution, row IFFT) runs entirely on chip, global memory holds only the
 // two shifted fields per block and the partial sums.
 // --------------------------------------------------------------------------
-constexpr int kThreadsI3Smem = 512;
+constexpr int kThreadsI3Smem = 1024;
 
 template <int n>
 __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const float2* what, const float2* wfine, float2* K3part,
