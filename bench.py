@@ -12,6 +12,7 @@ Prints one JSON line (rank 0).  Metric: C[W] cell*k-pts/s
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --mode collide [--cells C]   # time C[W] alone on the first C cells
+  python bench.py --mode vjp [--cells C]       # time the collision VJP alone
 
 --mode collide (not the benchmark line; used for profiling) times only the
 collision operator, one evaluation of the first C cells per step.
@@ -221,13 +222,15 @@ def run_ours(args):
     g.build()
     from paper_1408_1782_gb300 import decomp, inputs, qbe
 
-    if args.workload == "batched_16":
-        return run_batched(args, local)
+    if args.workload in ("batched_16", "batched_64"):
+        return run_batched(args, local, full=args.workload == "batched_64")
     if args.workload == "adjoint_n64":
         return run_adjoint(args, local)
     wl = workload(args.workload, args.precision)
     if args.mode == "collide":
         return run_collide_only(args, wl, local)
+    if args.mode == "vjp":
+        return run_vjp_only(args, wl, local)
     N, Nx = wl["N"], wl["Nx"]
     prec = wl.get("precision", 0)
     stream = torch.cuda.current_stream()
@@ -395,8 +398,10 @@ def fp32_split_report(wl, W0, local, qbe, torch, np):
     return out
 
 
-def run_batched(args, local):
-    """16 independent simulations stepped with one CUDA graph launch per split step."""
+def run_batched(args, local, full=False):
+    """Independent simulations stepped with one CUDA graph launch per split step: 16 drawn with
+    N in {32, 48, 64}, Nx in [16, 64] (batched_16), or the full mix of 64 with N in
+    {32, 48, 64, 96, 128}, Nx in [16, 256] (batched_64)."""
     import numpy as np
     import torch
 
@@ -409,9 +414,12 @@ def run_batched(args, local):
     stream = torch.cuda.current_stream()
     sims, desc = [], []
     units = 0
-    for i in range(16):
-        N = int(rng.choice([32, 48, 64]))
-        Nx = int(rng.integers(16, 65))
+    nsims = 64 if full else 16
+    grids = [32, 48, 64, 96, 128] if full else [32, 48, 64]
+    nx_max = 257 if full else 65
+    for i in range(nsims):
+        N = int(rng.choice(grids))
+        Nx = int(rng.integers(16, nx_max))
         bc = str(rng.choice(["periodic", "dirichlet", "maxwell"]))
         B = rng.normal(size=3)
         B *= rng.uniform(0, 1) / np.linalg.norm(B)
@@ -425,7 +433,7 @@ def run_batched(args, local):
         desc.append(f"{N}/{Nx}/{bc[0]}")
         units += 2 * Nx * N * N
     b = qbe.Batch(sims, stream=stream)
-    shapes = b.autotune()
+    shapes = b.autotune() if not full else []
     dt = 0.005
     b.step(dt, args.warmup)            # first call captures the graph
     torch.cuda.synchronize()
@@ -435,13 +443,15 @@ def run_batched(args, local):
     e1.record(stream)
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
-    line = {"workload": "batched_16", "metric": "C[W] cell·k-pts/s", "value": units * args.steps / (t_ms * 1e-3),
+    line = {"workload": "batched_64" if full else "batched_16", "metric": "C[W] cell·k-pts/s",
+            "value": units * args.steps / (t_ms * 1e-3),
             "unit": "cell·k-pts/s", "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "dtype": "f32-split", "graph_launches_per_step": 1,
             "sims": desc, "tuned_i3_shapes": [[gg, mm, round(ms, 3)] for gg, mm, ms in shapes],
-            "note": ("16 simulations drawn from the batching configuration's distributions with N in {32,48,64} "
-                     "and Nx in [16,64] (the full 64-simulation mix with N up to 128, Nx up to 256 needs about "
-                     "100 s per step on one GB300)")}
+            "note": ("the batching configuration: 64 simulations, N from {32,48,64,96,128}, Nx from [16,256], "
+                     "mixed walls, random |B| <= 1, default launch shapes" if full else
+                     "16 simulations drawn from the batching configuration's distributions with N in {32,48,64} "
+                     "and Nx in [16,64]; --workload batched_64 runs the full 64-simulation mix")}
     print(json.dumps(line), flush=True)
     b.close()
     for s in sims:
@@ -652,6 +662,44 @@ def adjoint_cpu_baseline(wl):
             "sample": f"one directional derivative of C[W] for 1 cell (N={wl['N']}, J=M={wl['J']}), {dt:.1f} s"}
 
 
+def run_vjp_only(args, wl, local):
+    """Collision VJPs (dC/dW)^T lam of the first `cells` cells of the workload's initial state."""
+    import torch
+
+    from paper_1408_1782_gb300 import inputs, qbe
+
+    N = wl["N"]
+    cells = args.cells or wl["Nx"]
+    stream = torch.cuda.current_stream()
+    s = qbe.Solver(N, cells, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream,
+                   precision=wl.get("precision", 0))
+    W = inputs.synthetic_w(N, wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])[:cells]
+    w = torch.from_numpy(W.copy()).cuda()
+    lam = torch.from_numpy(inputs.random_field(W.shape, seed=1)).cuda()
+    g = torch.empty_like(w)
+    for _ in range(args.warmup):
+        s.collide_vjp(w, lam, out=g)
+    torch.cuda.synchronize()
+    s.enable_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.collide_vjp(w, lam, out=g)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    v_ms, v_n = s.kernel_time("vjp_i3")
+    flops = cells * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N)
+    line = {"mode": "vjp", "metric": "dC/dW^T products, cell·k-pts/s", "value": args.steps * cells * N * N / (t_ms * 1e-3),
+            "unit": "cell·k-pts/s", "cells": cells, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_product": t_ms / args.steps, "vjp_i3_ms_per_launch": v_ms / max(v_n, 1),
+            "vjp_i3_tflops": flops / (v_ms / max(v_n, 1) * 1e-3) / 1e12,
+            "dtype": "f64" if wl.get("precision", 0) == 0 else "f32-split", "workload": wl["name"]}
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -660,8 +708,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "collide"], default="step")
-    ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128", "batched_16", "adjoint_n64"],
+    ap.add_argument("--mode", choices=["step", "collide", "vjp"], default="step")
+    ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128", "batched_16", "batched_64",
+                                           "adjoint_n64"],
                     default="plain_fp64_n64")
     ap.add_argument("--horizon", type=int, default=0,
                     help="adjoint_n64: split steps per gradient (default: one checkpoint segment, 20)")
