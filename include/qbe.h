@@ -180,6 +180,14 @@ int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_e
  * QBE_ERR_ARG, QBE_ERR_ALLOC, QBE_ERR_CUDA. */
 int qbe_step_vjp(qbe_handle* h, const double* lam_final, double* lam_init, double* grad_B, int on_device);
 
+/* The same reverse sweep for ncot cotangents at once (e.g. the gradients of
+ * several observables): each segment is recomputed once and every cotangent
+ * is swept over its intermediate states.  lam_final, lam_init [ncot][Nx][4][N][N],
+ * grad_B [ncot][Nx][3] (may be NULL).  Results equal ncot calls of
+ * qbe_step_vjp.  Extra memory: two states per cotangent. */
+int qbe_step_vjp_n(qbe_handle* h, int ncot, const double* lam_final, double* lam_init, double* grad_B,
+                   int on_device);
+
 /* Final-time observables of a state w[Nx][4][N][N] (NULL: the solver
  * state): out[0] = P_z = dx dv^2 sum 2 w3 (total spin polarisation along z,
  * tr(sigma_3 W) = 2 w3), out[1] = Phi_E = dx dv^2 sum v_x |v|^2/2 2 w0

@@ -66,6 +66,7 @@ struct qbe_handle {
   DevBuf snaps;                // [every][2 sA + 2] states of one segment
   DevBuf adj;                  // [5] states: two cotangent buffers, G1, lF0, final state
   DevBuf small;                // gsum[2], gbar[2], obs_out[2], gB[Nx][3], obs_part[Nx][2]
+  DevBuf gradb;                // [ncot][Nx][3] field gradients of a reverse sweep
 };
 
 namespace {
@@ -295,7 +296,7 @@ void qbe_destroy(qbe_handle* h) {
   cudaFree(h->mom); cudaFree(h->fbar); cudaFree(h->phiL); cudaFree(h->phiR);
   free_vjp_work(h->vw);
   cudaFree(h->lbuf);
-  h->ckpt.release(); h->snaps.release(); h->adj.release(); h->small.release();
+  h->ckpt.release(); h->snaps.release(); h->adj.release(); h->small.release(); h->gradb.release();
   delete h;
 }
 
@@ -531,59 +532,72 @@ int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_e
   return QBE_OK;
 }
 
-int qbe_step_vjp(qbe_handle* h, const double* lam_final, double* lam_init, double* grad_B, int on_device) {
+int qbe_step_vjp_n(qbe_handle* h, int ncot, const double* lam_final, double* lam_init, double* grad_B,
+                   int on_device) {
   if (!h) return QBE_ERR_ARG;
-  if (!lam_final || !lam_init) return fail(h, QBE_ERR_ARG, "step_vjp: null cotangent");
+  if (ncot < 1 || !lam_final || !lam_init) return fail(h, QBE_ERR_ARG, "step_vjp: ncot < 1 or null cotangent");
   if (!h->tape_valid) return fail(h, QBE_ERR_STATE, "no valid tape (call qbe_step_checkpointed first)");
   DeviceGuard dg(h->g.device);
   const int Nx = h->g.Nx;
   const double dt = h->tape_dt;
   const int nsteps = h->tape_nsteps, every = h->tape_every;
   const size_t S = state_elems(h);
+  const size_t nb3 = (size_t)Nx * 3;
   const int sA = half_substeps(h, dt);
   const size_t per_step = (size_t)(2 * sA + 2) * S;
   int r = ensure_vjp(h);
   if (r) return r;
-  if (h->snaps.ensure((size_t)every * per_step) != cudaSuccess || h->adj.ensure(5 * S) != cudaSuccess ||
-      h->small.ensure(small_elems(h)) != cudaSuccess)
+  if (h->snaps.ensure((size_t)every * per_step) != cudaSuccess ||
+      h->adj.ensure((2 * (size_t)ncot + 3) * S) != cudaSuccess || h->small.ensure(small_elems(h)) != cudaSuccess ||
+      h->gradb.ensure((size_t)ncot * nb3) != cudaSuccess)
     return fail(h, QBE_ERR_ALLOC, "adjoint sweep storage");
-  double* lam = h->adj.p;
-  double* tmp = h->adj.p + S;
-  double* G1 = h->adj.p + 2 * S;
-  double* lF0 = h->adj.p + 3 * S;
-  double* Wfin = h->adj.p + 4 * S;
+  // per cotangent k: lam[k], tmp[k] (ping-pong); shared: G1, lF0, the final state
+  std::vector<double*> lam(ncot), tmp(ncot);
+  for (int k = 0; k < ncot; ++k) {
+    lam[k] = h->adj.p + (size_t)(2 * k) * S;
+    tmp[k] = h->adj.p + (size_t)(2 * k + 1) * S;
+  }
+  double* G1 = h->adj.p + (size_t)(2 * ncot) * S;
+  double* lF0 = G1 + S;
+  double* Wfin = lF0 + S;
   double* gsum = h->small.p;
-  double* gB = h->small.p + 6;
   const size_t sb = S * sizeof(double);
-  cudaError_t e = cudaMemcpyAsync(lam, lam_final, sb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                  h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(gB, 0, (size_t)Nx * 3 * sizeof(double), h->stream);
+  const cudaMemcpyKind in_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind out_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaMemsetAsync(h->gradb.p, 0, (size_t)ncot * nb3 * sizeof(double), h->stream);
+  for (int k = 0; k < ncot && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(lam[k], lam_final + (size_t)k * S, sb, in_kind, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(Wfin, h->W, sb, cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "step_vjp setup");
   const int nseg = (nsteps + every - 1) / every;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int s0 = seg * every;
     const int len = (nsteps - s0) < every ? (nsteps - s0) : every;
-    // recompute the segment from its checkpoint, recording every step's intermediate states
+    // recompute the segment from its checkpoint once, recording every step's intermediate states
     e = cudaMemcpyAsync(h->W, h->ckpt.p + (size_t)seg * S, sb, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "restore checkpoint");
     for (int i = 0; i < len; ++i) {
       r = do_step(h, dt, h->snaps.p + (size_t)i * per_step);
       if (r) return r;
     }
-    for (int i = len - 1; i >= 0; --i) {
-      r = step_vjp_one(h, dt, h->snaps.p + (size_t)i * per_step, &lam, &tmp, G1, lF0, gB, gsum);
-      if (r) return r;
-    }
+    for (int i = len - 1; i >= 0; --i)
+      for (int k = 0; k < ncot; ++k) {
+        r = step_vjp_one(h, dt, h->snaps.p + (size_t)i * per_step, &lam[k], &tmp[k], G1, lF0,
+                         h->gradb.p + (size_t)k * nb3, gsum);
+        if (r) return r;
+      }
   }
   e = cudaMemcpyAsync(h->W, Wfin, sb, cudaMemcpyDeviceToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(lam_init, lam, sb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  for (int k = 0; k < ncot && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(lam_init + (size_t)k * S, lam[k], sb, out_kind, h->stream);
   if (e == cudaSuccess && grad_B)
-    e = cudaMemcpyAsync(grad_B, gB, (size_t)Nx * 3 * sizeof(double),
-                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+    e = cudaMemcpyAsync(grad_B, h->gradb.p, (size_t)ncot * nb3 * sizeof(double), out_kind, h->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(h->stream);
   return e == cudaSuccess ? QBE_OK : cuda_fail(h, e, "step_vjp output");
+}
+
+int qbe_step_vjp(qbe_handle* h, const double* lam_final, double* lam_init, double* grad_B, int on_device) {
+  return qbe_step_vjp_n(h, 1, lam_final, lam_init, grad_B, on_device);
 }
 
 int qbe_observables(qbe_handle* h, const double* w, double* out, int on_device) {

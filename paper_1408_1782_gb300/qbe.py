@@ -63,6 +63,7 @@ SIGNATURES = {
     "qbe_collide_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int, _c_int]),
     "qbe_step_checkpointed": (_c_int, [_c_void_p, _c_double, _c_int, _c_int]),
     "qbe_step_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int]),
+    "qbe_step_vjp_n": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_observables": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_observables_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_entropy": (_c_int, [_c_void_p, _c_void_p, _c_int]),
@@ -339,6 +340,21 @@ class Solver:
         if not (dev == dev2 == dev3):
             raise ValueError("cotangents must all be host or all be device memory")
         self._check(lib().qbe_step_vjp(self._h, _c_void_p(pl), _c_void_p(po), _c_void_p(pb), dev), "qbe_step_vjp")
+        return out, grad_B
+
+    def step_vjp_many(self, lams, out=None, grad_B=None):
+        """step_vjp for a stack of cotangents lams[ncot][Nx][4][N][N] in one reverse sweep."""
+        ncot = lams.shape[0]
+        shape = (ncot,) + self.state_shape
+        pl, dev, k1 = _arg(lams, shape)
+        out = self._like(lams, shape, out)
+        grad_B = self._like(lams, (ncot, self.Nx, 3), grad_B)
+        po, dev2, k2 = _arg(out, shape)
+        pb, dev3, k3 = _arg(grad_B, (ncot, self.Nx, 3))
+        if not (dev == dev2 == dev3):
+            raise ValueError("cotangents must all be host or all be device memory")
+        self._check(lib().qbe_step_vjp_n(self._h, ncot, _c_void_p(pl), _c_void_p(po), _c_void_p(pb), dev),
+                    "qbe_step_vjp_n")
         return out, grad_B
 
     def observables(self, w=None, out=None):

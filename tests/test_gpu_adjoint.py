@@ -319,3 +319,20 @@ def test_autograd_functions(qbe):
     assert np.abs(w.grad.cpu().numpy() - ref).max() <= 1e-14 * np.abs(ref).max()
     del other
     s.close()
+
+
+def test_step_vjp_for_several_cotangents_in_one_sweep(qbe):
+    """One reverse sweep for both observables equals two single sweeps, bitwise."""
+    N, Nx, J, M = 8, 4, 4, 2
+    W = inputs.synthetic_w(N, Nx, seed=97, perturb=0.05)
+    B = inputs.uniform_b(Nx, (0.1, -0.3, 0.2))
+    s = gpu_solver(qbe, N, Nx, J, M, "maxwell", R=2.0)
+    s.set_state(W)
+    s.set_bfield(B)
+    s.step_checkpointed(0.01, 5, 2)
+    lams = np.stack([s.observables_vjp(np.array([1.0, 0.0])), s.observables_vjp(np.array([0.0, 1.0]))])
+    l0, gb = s.step_vjp_many(lams)
+    for k in range(2):
+        a, b = s.step_vjp(lams[k].copy())
+        assert np.array_equal(a, l0[k]) and np.array_equal(b, gb[k])
+    s.close()
