@@ -240,8 +240,28 @@ __global__ void __launch_bounds__(kThreads) k_i24(const typename Vec2Of<T>::type
 // The unit's partial sum acc[2][n*n] (pairs (0,1), (2,3), real space) is
 // written to its own slot of K3part and reduced in fixed order later.
 // --------------------------------------------------------------------------
+// Launch shape of the staged I3 kernel: three 256-thread blocks per SM with 64 KB chunks, except
+// FP32 on padded grids above 128 points (where the field does not fit one block's shared memory):
+// one 1024-thread block per SM with 128 KB chunks, more warps to hide the scratch round trips.
 template <int n, class T>
-__global__ void __launch_bounds__(kThreads, 3) k_i3(const typename Vec2Of<T>::type* what,
+__host__ __device__ constexpr bool i3_wide() {
+  return std::is_same<T, float>::value && n > 128;
+}
+template <int n, class T>
+__host__ __device__ constexpr int i3_threads() {
+  return i3_wide<n, T>() ? 1024 : kThreads;
+}
+template <int n, class T>
+__host__ __device__ constexpr int i3_min_blocks() {
+  return i3_wide<n, T>() ? 1 : 3;
+}
+template <int n, class T>
+__host__ __device__ constexpr int i3_chunk_bytes() {
+  return i3_wide<n, T>() ? 131072 : 65536;
+}
+
+template <int n, class T>
+__global__ void __launch_bounds__(i3_threads<n, T>(), i3_min_blocks<n, T>()) k_i3(const typename Vec2Of<T>::type* what,
                                                     const typename Vec2Of<T>::type* wfine,
                                                     typename Vec2Of<T>::type* K3part, typename Vec2Of<T>::type* ws,
                                                     const typename Vec2Of<T>::type* __restrict__ gtw,
@@ -284,11 +304,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_i3(const typename Vec2Of<T>::ty
         const C2* in = what + ((size_t)c * 4 + p) * P;
         C2* S = Sig + (size_t)p * P;
         // only the n/2 columns (y frequencies) of Xi are non-zero: transform those
-        col_pass_list<n, 1, false, 0>(
+        col_pass_list<n, 1, false, 0, i3_chunk_bytes<n, T>()>(
             sm, tw, xcols, n / 2,
             [&](int ix, int iy) { return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<T>(); },
             NoMid(), [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
-        row_pass<n, 1, false, 0>(
+        row_pass<n, 1, false, 0, i3_chunk_bytes<n, T>()>(
             sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : zero2<T>(); }, NoMid(),
             [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
       }
@@ -300,18 +320,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_i3(const typename Vec2Of<T>::ty
         for (int p = 0; p < 2; ++p) {
           const C2* Sp = Sig + (size_t)p * P;
           C2* accp = acc + (size_t)p * P;
-          row_pass<n, -1, false, 0>(
+          row_pass<n, -1, false, 0, i3_chunk_bytes<n, T>()>(
               sm, tw,
               [&](int ix, int iy) {
                 const C2 z = wa[ix * n + iy];
                 return cscale(Sp[ix * n + iy], im ? z.y : z.x);
               },
               NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
-          col_conv_pass<n>(
+          col_conv_pass<n, i3_chunk_bytes<n, T>()>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
               [&](int ix, int iy) { return psp[ix * n + iy]; },
               [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
-          row_pass<n, 1, false, 0>(
+          row_pass<n, 1, false, 0, i3_chunk_bytes<n, T>()>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
               [&](int ix, int iy, C2 v) {
                 const C2 s = Sa[ix * n + iy];
@@ -532,6 +552,12 @@ size_t smem_bytes() {
 }
 
 template <int n, class T>
+size_t i3_staged_smem_bytes() {
+  using C2 = typename Vec2Of<T>::type;
+  return (size_t)(n + Chunk<n, sizeof(C2), i3_chunk_bytes<n, T>()>::SMEM_ELEMS) * sizeof(C2);
+}
+
+template <int n, class T>
 void set_smem_attributes() {
   static bool done = false;
   if (done) return;
@@ -539,7 +565,7 @@ void set_smem_attributes() {
   cudaFuncSetAttribute(k_prep<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i1<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i24<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_i3<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_i3<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_staged_smem_bytes<n, T>());
   cudaFuncSetAttribute(k_assemble<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     cudaFuncSetAttribute(k_i3_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
@@ -553,7 +579,7 @@ int i3_blocks_per_sm() {
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>());
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n, T>, kThreads, smem_bytes<n, T>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n, T>, i3_threads<n, T>(), i3_staged_smem_bytes<n, T>());
   return b < 1 ? 1 : b;
 }
 
@@ -589,8 +615,9 @@ cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w,
     k_i3_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(what, wfine, K3part, ws, tb.tw, tb.psip_s, tb.phase,
                                                                   t.J, t.M, cw.nmc, cw.mch, nunits);
   else
-    k_i3<n, T><<<grid, kThreads, sm, s>>>(what, wfine, K3part, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M, cw.nmc,
-                                          cw.mch, nunits);
+    k_i3<n, T><<<grid, i3_threads<n, T>(), i3_staged_smem_bytes<n, T>(), s>>>(what, wfine, K3part, ws, tb.tw,
+                                                                             tb.psip_s, tb.phase, t.J, t.M, cw.nmc,
+                                                                             cw.mch, nunits);
   end();
   begin(KG_ASSEMBLE);
   k_assemble<n, T><<<ncells, kThreads, sm, s>>>(wfine, Dacc, K2acc, K4acc, K3part, t.J * cw.nmc, ws, tb.tw, c);

@@ -331,8 +331,8 @@ __host__ __device__ constexpr int largest_divisor_le(int n, int cap) {
   return cap >= n ? n : (n % cap == 0 ? cap : largest_divisor_le(n, cap - 1));
 }
 
-template <int n, int ELEM = 16> struct Chunk {
-  static constexpr int RC0 = 65536 / (n * ELEM);
+template <int n, int ELEM = 16, int CB = 65536> struct Chunk {
+  static constexpr int RC0 = CB / (n * ELEM);
   static constexpr int RC = largest_divisor_le(n, RC0);
   static constexpr int CC = RC;
   static constexpr int LS = n + 1;                 // padded row stride (odd => no bank conflicts)
@@ -342,9 +342,9 @@ template <int n, int ELEM = 16> struct Chunk {
 // Row pass over an n x n field (rows = fixed ix, transform along iy):
 // for each chunk: sm[r][iy] = ld(ix, iy); [FFT DIR1]; [sm = mid(ix, iy, sm)]; [FFT DIR2]; st(ix, iy, sm).
 // DIR = 0 skips that transform; HAS_MID selects the pointwise middle step.
-template <int n, int DIR1, bool HAS_MID, int DIR2, class C2, class LD, class MID, class ST>
+template <int n, int DIR1, bool HAS_MID, int DIR2, int CB = 65536, class C2, class LD, class MID, class ST>
 __device__ __forceinline__ void row_pass(C2* sm, const C2* tw, LD ld, MID mid, ST st) {
-  constexpr int RC = Chunk<n, sizeof(C2)>::RC, LS = Chunk<n, sizeof(C2)>::LS;
+  constexpr int RC = Chunk<n, sizeof(C2), CB>::RC, LS = Chunk<n, sizeof(C2), CB>::LS;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int r0 = 0; r0 < n; r0 += RC) {
 #pragma unroll 4
@@ -373,9 +373,9 @@ __device__ __forceinline__ void row_pass(C2* sm, const C2* tw, LD ld, MID mid, S
 }
 
 // Column pass (transform along ix) over chunks of CC columns held as sm[ix][c].
-template <int n, int DIR1, bool HAS_MID, int DIR2, class C2, class LD, class MID, class ST>
+template <int n, int DIR1, bool HAS_MID, int DIR2, int CB = 65536, class C2, class LD, class MID, class ST>
 __device__ __forceinline__ void col_pass(C2* sm, const C2* tw, LD ld, MID mid, ST st) {
-  constexpr int CC = Chunk<n, sizeof(C2)>::CC;
+  constexpr int CC = Chunk<n, sizeof(C2), CB>::CC;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < n; c0 += CC) {
 #pragma unroll 4
@@ -405,9 +405,9 @@ __device__ __forceinline__ void col_pass(C2* sm, const C2* tw, LD ld, MID mid, S
 
 // Column pass doing a circular convolution along ix for each column iy:
 // sm[ix][c] = ld(ix, iy); forward FFT; times mul(pos_x, iy); inverse FFT; st(ix, iy, value).
-template <int n, class C2, class LD, class MUL, class ST>
+template <int n, int CB = 65536, class C2, class LD, class MUL, class ST>
 __device__ __forceinline__ void col_conv_pass(C2* sm, const C2* tw, LD ld, MUL mul, ST st) {
-  constexpr int CC = Chunk<n, sizeof(C2)>::CC;
+  constexpr int CC = Chunk<n, sizeof(C2), CB>::CC;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < n; c0 += CC) {
 #pragma unroll 4
@@ -427,10 +427,10 @@ __device__ __forceinline__ void col_conv_pass(C2* sm, const C2* tw, LD ld, MUL m
 }
 
 // Column pass over a subset of columns cols[0..ncols) (chunks of CC columns).
-template <int n, int DIR1, bool HAS_MID, int DIR2, class C2, class LD, class MID, class ST>
+template <int n, int DIR1, bool HAS_MID, int DIR2, int CB = 65536, class C2, class LD, class MID, class ST>
 __device__ __forceinline__ void col_pass_list(C2* sm, const C2* tw, const int* cols, int ncols, LD ld, MID mid,
                                               ST st) {
-  constexpr int CC = Chunk<n, sizeof(C2)>::CC;
+  constexpr int CC = Chunk<n, sizeof(C2), CB>::CC;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int c0 = 0; c0 < ncols; c0 += CC) {
     const int nc = (ncols - c0) < CC ? (ncols - c0) : CC;
