@@ -63,6 +63,7 @@ cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int
   cw.prec = prec;
   cw.nb = nb;
   cw.grid_i3 = nsm * bps;
+  cw.grid_max = cw.grid_i3;
   // enough (cell, j, m-chunk) units for about 8 waves of the persistent grid
   int nmc = (8 * cw.grid_i3 + nb * t.J - 1) / (nb * t.J);
   if (nmc < 1) nmc = 1;
@@ -124,6 +125,46 @@ int vjp_bps(const Tables& t, int prec) {
   return 0;
 }
 }  // namespace
+
+cudaError_t collide_pre(const Tables& t, CollisionWork& cw, const double* w, int ncells, cudaStream_t s,
+                        long long& launches) {
+#define QBE_PRE_CALL(n, T) collide_pre_n<n, T>(t, cw, w, ncells, s, launches, nullptr)
+  if (cw.prec == 1) {
+    QBE_VJP_SWITCH(float, QBE_PRE_CALL)
+  } else {
+    QBE_VJP_SWITCH(double, QBE_PRE_CALL)
+  }
+#undef QBE_PRE_CALL
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t collide_post(const Tables& t, CollisionWork& cw, double* c, int ncells, cudaStream_t s,
+                         long long& launches) {
+#define QBE_POST_CALL(n, T) collide_post_n<n, T>(t, cw, c, ncells, s, launches, nullptr)
+  if (cw.prec == 1) {
+    QBE_VJP_SWITCH(float, QBE_POST_CALL)
+  } else {
+    QBE_VJP_SWITCH(double, QBE_POST_CALL)
+  }
+#undef QBE_POST_CALL
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t i3_group(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
+                     void* ws, int grid, cudaStream_t s, long long& launches) {
+  if (njobs < 1) return cudaErrorInvalidValue;
+  const Tables& t = *tabs[0];
+  for (int k = 1; k < njobs; ++k)
+    if (tabs[k]->n != t.n || cws[k]->prec != cws[0]->prec) return cudaErrorInvalidValue;
+#define QBE_GROUP_CALL(n, T) i3_group_n<n, T>(tabs, cws, ncells, njobs, ws, grid, s, launches)
+  if (cws[0]->prec == 1) {
+    QBE_VJP_SWITCH(float, QBE_GROUP_CALL)
+  } else {
+    QBE_VJP_SWITCH(double, QBE_GROUP_CALL)
+  }
+#undef QBE_GROUP_CALL
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
                         double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,

@@ -63,6 +63,14 @@ __device__ __forceinline__ typename Vec2Of<T>::type zero2() {
   return mk2((T)0, (T)0);
 }
 
+// Job of a global I3 unit: the last job whose first unit is <= gunit (uniform across the block).
+template <class T>
+__device__ __forceinline__ int i3_job_of(const I3Jobs<T>& jobs, int gunit) {
+  int k = 0;
+  while (k + 1 < jobs.njobs && gunit >= jobs.job[k + 1].unit_begin) ++k;
+  return k;
+}
+
 // --------------------------------------------------------------------------
 // Prep: Xi coefficients of the four Pauli components (paired) and the
 // fine-grid interpolants.  One block per cell.
@@ -261,13 +269,8 @@ __host__ __device__ constexpr int i3_chunk_bytes() {
 }
 
 template <int n, class T>
-__global__ void __launch_bounds__(i3_threads<n, T>(), i3_min_blocks<n, T>()) k_i3(const typename Vec2Of<T>::type* what,
-                                                    const typename Vec2Of<T>::type* wfine,
-                                                    typename Vec2Of<T>::type* K3part, typename Vec2Of<T>::type* ws,
-                                                    const typename Vec2Of<T>::type* __restrict__ gtw,
-                                                    const T* __restrict__ psip_s,
-                                                    const typename Vec2Of<T>::type* __restrict__ phase, int J, int M,
-                                                    int nmc, int mch, int nunits) {
+__global__ void __launch_bounds__(i3_threads<n, T>(), i3_min_blocks<n, T>())
+    k_i3(const I3Jobs<T> jobs, typename Vec2Of<T>::type* ws, const typename Vec2Of<T>::type* __restrict__ gtw) {
   using C2 = typename Vec2Of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
@@ -288,14 +291,20 @@ __global__ void __launch_bounds__(i3_threads<n, T>(), i3_min_blocks<n, T>()) k_i
   C2* slot = ws + (size_t)blockIdx.x * 3 * P;
   C2* Sig = slot;           // [2][P]
   C2* G = slot + 2 * P;
-  for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+  for (int gunit = blockIdx.x; gunit < jobs.total; gunit += gridDim.x) {
+    const I3Job<T>& jb = jobs.job[i3_job_of(jobs, gunit)];
+    const int unit = gunit - jb.unit_begin;
+    const int J = jb.J, M = jb.M, nmc = jb.nmc, mch = jb.mch;
+    const C2* what = jb.what;
+    const T* __restrict__ psip_s = jb.psip_s;
+    const C2* __restrict__ phase = jb.phase;
     const int c = unit / (J * nmc);
     const int j = (unit / nmc) % J;
     const int mc = unit % nmc;
-    C2* acc = K3part + (size_t)unit * 2 * P;
+    C2* acc = jb.K3part + (size_t)unit * 2 * P;
     zero_fields(acc, 2 * P);
     const T* psp = psip_s + (size_t)j * P;
-    const C2* wf = wfine + (size_t)c * 2 * P;
+    const C2* wf = jb.wfine + (size_t)c * 2 * P;
     const int m0 = mc * mch, m1 = min(M, m0 + mch);
     for (int m = m0; m < m1; ++m) {
       const C2* px = phase + ((size_t)j * M + m) * 2 * n;
@@ -356,11 +365,8 @@ __global__ void __launch_bounds__(i3_threads<n, T>(), i3_min_blocks<n, T>()) k_i
 constexpr int kThreadsI3Smem = 1024;
 
 template <int n>
-__global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const float2* what, const float2* wfine, float2* K3part,
-                                                             float2* ws, const float2* __restrict__ gtw,
-                                                             const float* __restrict__ psip_s,
-                                                             const float2* __restrict__ phase, int J, int M, int nmc,
-                                                             int mch, int nunits) {
+__global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const I3Jobs<float> jobs, float2* ws,
+                                                             const float2* __restrict__ gtw) {
   using C2 = float2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
@@ -375,11 +381,17 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const float2* wha
   }
   load_twiddles<n>(tw, gtw);
   C2* Sig = ws + (size_t)blockIdx.x * 3 * P;   // [2][P]
-  for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+  for (int gunit = blockIdx.x; gunit < jobs.total; gunit += gridDim.x) {
+    const I3Job<float>& jb = jobs.job[i3_job_of(jobs, gunit)];
+    const int unit = gunit - jb.unit_begin;
+    const int J = jb.J, M = jb.M, nmc = jb.nmc, mch = jb.mch;
+    const C2* what = jb.what;
+    const float* __restrict__ psip_s = jb.psip_s;
+    const C2* __restrict__ phase = jb.phase;
     const int c = unit / (J * nmc);
     const int j = (unit / nmc) % J;
     const int mc = unit % nmc;
-    C2* acc = K3part + (size_t)unit * 2 * P;
+    C2* acc = jb.K3part + (size_t)unit * 2 * P;
     zero_fields(acc, 2 * P);
     {
       const float4* src = reinterpret_cast<const float4*>(psip_s + (size_t)j * P);
@@ -387,7 +399,7 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const float2* wha
       for (int i4 = threadIdx.x; i4 < P / 4; i4 += blockDim.x) dst[i4] = src[i4];
       __syncthreads();
     }
-    const C2* wf = wfine + (size_t)c * 2 * P;
+    const C2* wf = jb.wfine + (size_t)c * 2 * P;
     const int m0 = mc * mch, m1 = min(M, m0 + mch);
     for (int m = m0; m < m1; ++m) {
       const C2* px = phase + ((size_t)j * M + m) * 2 * n;
@@ -583,18 +595,17 @@ int i3_blocks_per_sm() {
   return b < 1 ? 1 : b;
 }
 
+// The collision operator in three parts: the per-cell terms before I3 (prep, I1, I2/I4), the I3
+// launch (a work queue over the units of one or several simulations of the same padded size), and
+// the per-cell assembly.  collide_batch_n runs all three for one simulation.
 template <int n, class T>
-cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells,
-                            cudaStream_t s, long long& launches, KernelTimer* tm) {
+cudaError_t collide_pre_n(const Tables& t, CollisionWork& cw, const double* w, int ncells, cudaStream_t s,
+                          long long& launches, KernelTimer* tm) {
   using C2 = typename Vec2Of<T>::type;
   set_smem_attributes<n, T>();
   const TabPtrs<T> tb = tab_ptrs<T>(t);
   C2* what = (C2*)cw.what;
   C2* wfine = (C2*)cw.wfine;
-  C2* Dacc = (C2*)cw.Dacc;
-  T* K2acc = (T*)cw.K2acc;
-  C2* K4acc = (C2*)cw.K4acc;
-  C2* K3part = (C2*)cw.K3part;
   C2* ws = (C2*)cw.ws;
   const size_t sm = smem_bytes<n, T>();
   auto begin = [&](int g) { if (tm) tm->begin(g, s); };
@@ -603,27 +614,88 @@ cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w,
   k_prep<n, T><<<ncells, kThreads, sm, s>>>(w, what, wfine, ws, tb.tw);
   end();
   begin(KG_I1);
-  k_i1<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, Dacc, ws, tb.tw, tb.phip, tb.Ktab, t.J);
+  k_i1<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, (C2*)cw.Dacc, ws, tb.tw, tb.phip, tb.Ktab, t.J);
   end();
   begin(KG_I24);
-  k_i24<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, K2acc, K4acc, ws, tb.tw, tb.psi, t.J);
+  k_i24<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, (T*)cw.K2acc, (C2*)cw.K4acc, ws, tb.tw, tb.psi, t.J);
   end();
-  const int nunits = ncells * t.J * cw.nmc;
-  const int grid = nunits < cw.grid_i3 ? nunits : cw.grid_i3;
-  begin(KG_I3);
-  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
-    k_i3_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(what, wfine, K3part, ws, tb.tw, tb.psip_s, tb.phase,
-                                                                  t.J, t.M, cw.nmc, cw.mch, nunits);
-  else
-    k_i3<n, T><<<grid, i3_threads<n, T>(), i3_staged_smem_bytes<n, T>(), s>>>(what, wfine, K3part, ws, tb.tw,
-                                                                             tb.psip_s, tb.phase, t.J, t.M, cw.nmc,
-                                                                             cw.mch, nunits);
-  end();
-  begin(KG_ASSEMBLE);
-  k_assemble<n, T><<<ncells, kThreads, sm, s>>>(wfine, Dacc, K2acc, K4acc, K3part, t.J * cw.nmc, ws, tb.tw, c);
-  end();
-  launches += 5;
+  launches += 3;
   return cudaGetLastError();
+}
+
+template <int n, class T>
+I3Job<T> i3_job(const Tables& t, const CollisionWork& cw, int ncells, int unit_begin) {
+  using C2 = typename Vec2Of<T>::type;
+  const TabPtrs<T> tb = tab_ptrs<T>(t);
+  I3Job<T> jb;
+  jb.what = (const C2*)cw.what;
+  jb.wfine = (const C2*)cw.wfine;
+  jb.K3part = (C2*)cw.K3part;
+  jb.psip_s = tb.psip_s;
+  jb.phase = tb.phase;
+  jb.J = t.J;
+  jb.M = t.M;
+  jb.nmc = cw.nmc;
+  jb.mch = cw.mch;
+  jb.unit_begin = unit_begin;
+  jb.nunits = ncells * t.J * cw.nmc;
+  return jb;
+}
+
+// I3 over the units of njobs simulations (same n and precision, njobs <= kMaxI3Jobs); ws must hold
+// 3 (2N)^2 complex values for each of `grid` blocks.
+template <int n, class T>
+cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
+                       void* ws, int grid, cudaStream_t s, long long& launches) {
+  using C2 = typename Vec2Of<T>::type;
+  if (njobs < 1 || njobs > kMaxI3Jobs) return cudaErrorInvalidValue;
+  set_smem_attributes<n, T>();
+  I3Jobs<T> jobs;
+  jobs.njobs = njobs;
+  int total = 0;
+  for (int k = 0; k < njobs; ++k) {
+    jobs.job[k] = i3_job<n, T>(*tabs[k], *cws[k], ncells[k], total);
+    total += jobs.job[k].nunits;
+  }
+  jobs.total = total;
+  if (total == 0) return cudaSuccess;
+  const int g = total < grid ? total : grid;
+  const TabPtrs<T> tb = tab_ptrs<T>(*tabs[0]);
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+    k_i3_smem<n><<<g, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(jobs, (C2*)ws, tb.tw);
+  else
+    k_i3<n, T><<<g, i3_threads<n, T>(), i3_staged_smem_bytes<n, T>(), s>>>(jobs, (C2*)ws, tb.tw);
+  ++launches;
+  return cudaGetLastError();
+}
+
+template <int n, class T>
+cudaError_t collide_post_n(const Tables& t, CollisionWork& cw, double* c, int ncells, cudaStream_t s,
+                           long long& launches, KernelTimer* tm) {
+  using C2 = typename Vec2Of<T>::type;
+  set_smem_attributes<n, T>();
+  const TabPtrs<T> tb = tab_ptrs<T>(t);
+  if (tm) tm->begin(KG_ASSEMBLE, s);
+  k_assemble<n, T><<<ncells, kThreads, smem_bytes<n, T>(), s>>>((C2*)cw.wfine, (C2*)cw.Dacc, (T*)cw.K2acc,
+                                                                (C2*)cw.K4acc, (C2*)cw.K3part, t.J * cw.nmc,
+                                                                (C2*)cw.ws, tb.tw, c);
+  if (tm) tm->end(s);
+  ++launches;
+  return cudaGetLastError();
+}
+
+template <int n, class T>
+cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells,
+                            cudaStream_t s, long long& launches, KernelTimer* tm) {
+  cudaError_t e = collide_pre_n<n, T>(t, cw, w, ncells, s, launches, tm);
+  if (e != cudaSuccess) return e;
+  const Tables* tp = &t;
+  const CollisionWork* cp = &cw;
+  if (tm) tm->begin(KG_I3, s);
+  e = i3_group_n<n, T>(&tp, &cp, &ncells, 1, cw.ws, cw.grid_i3, s, launches);
+  if (tm) tm->end(s);
+  if (e != cudaSuccess) return e;
+  return collide_post_n<n, T>(t, cw, c, ncells, s, launches, tm);
 }
 
 }  // namespace qbe

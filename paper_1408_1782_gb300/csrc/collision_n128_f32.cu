@@ -8,4 +8,10 @@ template int i3_blocks_per_sm<128, float>();
 template cudaError_t collide_vjp_n<128, float>(const Tables&, CollisionWork&, VjpWork&, const double*, const double*,
                                             double*, int, int, cudaStream_t, long long&, KernelTimer*);
 template int i3_vjp_blocks_per_sm<128, float>();
+template cudaError_t collide_pre_n<128, float>(const Tables&, CollisionWork&, const double*, int, cudaStream_t,
+                                            long long&, KernelTimer*);
+template cudaError_t collide_post_n<128, float>(const Tables&, CollisionWork&, double*, int, cudaStream_t, long long&,
+                                             KernelTimer*);
+template cudaError_t i3_group_n<128, float>(const Tables* const*, const CollisionWork* const*, const int*, int, void*,
+                                         int, cudaStream_t, long long&);
 }  // namespace qbe

@@ -8,4 +8,10 @@ template int i3_blocks_per_sm<64, double>();
 template cudaError_t collide_vjp_n<64, double>(const Tables&, CollisionWork&, VjpWork&, const double*, const double*,
                                             double*, int, int, cudaStream_t, long long&, KernelTimer*);
 template int i3_vjp_blocks_per_sm<64, double>();
+template cudaError_t collide_pre_n<64, double>(const Tables&, CollisionWork&, const double*, int, cudaStream_t,
+                                            long long&, KernelTimer*);
+template cudaError_t collide_post_n<64, double>(const Tables&, CollisionWork&, double*, int, cudaStream_t, long long&,
+                                             KernelTimer*);
+template cudaError_t i3_group_n<64, double>(const Tables* const*, const CollisionWork* const*, const int*, int, void*,
+                                         int, cudaStream_t, long long&);
 }  // namespace qbe

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/qbe.h"
@@ -48,6 +49,28 @@ template <> inline TabPtrs<float> tab_ptrs<float>(const Tables& t) {
   return {t.tw_f, t.phip_f, t.Ktab_f, t.psi_f, t.psip_s_f, t.phase_f};
 }
 
+// One simulation's share of an I3 launch: the Hu-Ying kernels run a work queue over
+// the (cell, j, m-chunk) units of up to kMaxI3Jobs simulations of the same padded size
+// (passed by value as a kernel parameter).
+constexpr int kMaxI3Jobs = 64;
+template <class T>
+struct I3Job {
+  const typename std::conditional<sizeof(T) == 8, double2, float2>::type* what;
+  const typename std::conditional<sizeof(T) == 8, double2, float2>::type* wfine;
+  typename std::conditional<sizeof(T) == 8, double2, float2>::type* K3part;
+  const T* psip_s;
+  const typename std::conditional<sizeof(T) == 8, double2, float2>::type* phase;
+  int J, M, nmc, mch;
+  int unit_begin;   // first global unit of this simulation
+  int nunits;
+};
+template <class T>
+struct I3Jobs {
+  I3Job<T> job[kMaxI3Jobs];
+  int njobs;
+  int total;
+};
+
 // Per-evaluation buffers of the collision operator for a batch of nb cells.
 struct CollisionWork {
   int prec = 0;        // 0: FP64 transforms, 1: FP32 transforms (FP32-split form)
@@ -55,6 +78,7 @@ struct CollisionWork {
   int nmc = 1;         // m-chunks per (cell, j) unit of the I3 kernel
   int mch = 1;         // m values per chunk
   int grid_i3 = 0;     // persistent grid of the I3 kernel
+  int grid_max = 0;    // its occupancy limit (SMs x resident blocks)
   // buffers of the transform precision (complex = double2 or float2)
   void* what = nullptr;      // [nb][4][n*n] spectral pairs (w0+iw1, w2+iw3, w1+iw2, w3)
   void* wfine = nullptr;     // [nb][2][n*n] fine-grid fields (w0+iw1, w2+iw3)
@@ -159,6 +183,23 @@ cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w,
                             long long& launches, KernelTimer* tm);
 template <int n, class T>
 int i3_blocks_per_sm();
+// The collision operator in parts (collision_kernels.cuh): the per-cell terms before I3, the I3
+// work queue over one or several simulations of the same padded size, the per-cell assembly.
+cudaError_t collide_pre(const Tables& t, CollisionWork& cw, const double* w, int ncells, cudaStream_t s,
+                        long long& launches);
+cudaError_t collide_post(const Tables& t, CollisionWork& cw, double* c, int ncells, cudaStream_t s,
+                         long long& launches);
+cudaError_t i3_group(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
+                     void* ws, int grid, cudaStream_t s, long long& launches);
+template <int n, class T>
+cudaError_t collide_pre_n(const Tables& t, CollisionWork& cw, const double* w, int ncells, cudaStream_t s,
+                          long long& launches, KernelTimer* tm);
+template <int n, class T>
+cudaError_t collide_post_n(const Tables& t, CollisionWork& cw, double* c, int ncells, cudaStream_t s,
+                           long long& launches, KernelTimer* tm);
+template <int n, class T>
+cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
+                       void* ws, int grid, cudaStream_t s, long long& launches);
 void free_collision_work(CollisionWork& cw);
 
 // Vector-Jacobian product of the collision operator (collision_vjp.cuh):

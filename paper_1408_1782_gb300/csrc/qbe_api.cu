@@ -754,6 +754,111 @@ void drop_graph(qbe_batch* b) {
   b->graph = nullptr;
 }
 
+// One split step of every simulation, captured in phases: per-simulation branches run the
+// transport and the per-cell collision terms; between them, one I3 launch per padded-grid size and
+// precision runs a work queue over the (simulation, cell, j, m-chunk) units of all simulations of
+// that size (Sec. 3.2; the simulations are independent).  Per simulation the arithmetic is that of
+// do_step: the same kernels on the same units.
+int batch_capture_step(qbe_batch* b, double dt, cudaStream_t origin) {
+  const size_t ns = b->sims.size();
+  auto branch = [&](size_t i) { return origin == b->side[i] ? origin : b->side[i]; };
+  auto fork = [&]() {
+    cudaEventRecord(b->fork, origin);
+    for (size_t i = 0; i < ns; ++i)
+      if (branch(i) != origin) cudaStreamWaitEvent(branch(i), b->fork, 0);
+  };
+  auto join = [&]() {
+    for (size_t i = 0; i < ns; ++i)
+      if (branch(i) != origin) {
+        cudaEventRecord(b->join[i], branch(i));
+        cudaStreamWaitEvent(origin, b->join[i], 0);
+      }
+  };
+  // groups of simulations sharing the I3 kernel (padded size and precision), at most kMaxI3Jobs each
+  std::vector<std::vector<size_t>> groups;
+  for (size_t i = 0; i < ns; ++i) {
+    const qbe_handle* h = b->sims[i];
+    bool placed = false;
+    for (auto& g : groups) {
+      const qbe_handle* h0 = b->sims[g[0]];
+      if (h0->tab.n == h->tab.n && h0->cw.prec == h->cw.prec && (int)g.size() < kMaxI3Jobs) {
+        g.push_back(i);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) groups.push_back({i});
+  }
+  auto i3_all = [&](long long& launches) {
+    for (auto& g : groups) {
+      std::vector<const Tables*> tabs;
+      std::vector<const CollisionWork*> cws;
+      std::vector<int> nc;
+      for (size_t i : g) {
+        tabs.push_back(&b->sims[i]->tab);
+        cws.push_back(&b->sims[i]->cw);
+        nc.push_back(b->sims[i]->g.Nx);
+      }
+      const CollisionWork& c0 = b->sims[g[0]]->cw;
+      const int grid = (int)(c0.ws_fields / 3);           // blocks the first simulation's scratch can hold
+      const int gmax = c0.grid_max;
+      cudaError_t e = i3_group(tabs.data(), cws.data(), nc.data(), (int)g.size(), c0.ws, grid < gmax ? grid : gmax,
+                               origin, launches);
+      if (e != cudaSuccess) return QBE_ERR_CUDA;
+    }
+    return QBE_OK;
+  };
+  std::vector<cudaStream_t> saved(ns);
+  std::vector<bool> was_on(ns);
+  for (size_t i = 0; i < ns; ++i) {
+    qbe_handle* h = b->sims[i];
+    saved[i] = h->stream;
+    was_on[i] = h->timer.on;
+    h->timer.on = false;
+    h->stream = branch(i);
+  }
+  int r = QBE_OK;
+  long long& launches = b->sims[0]->launches;
+  // transport half step, first collision's per-cell terms
+  fork();
+  for (size_t i = 0; i < ns && !r; ++i) {
+    qbe_handle* h = b->sims[i];
+    r = do_advect(h, 0.5 * dt);
+    if (!r && collide_pre(h->tab, h->cw, h->W, h->g.Nx, h->stream, h->launches) != cudaSuccess) r = QBE_ERR_CUDA;
+  }
+  join();
+  if (!r) r = i3_all(launches);
+  // first collision's assembly, RK stage 1, second collision's per-cell terms
+  fork();
+  for (size_t i = 0; i < ns && !r; ++i) {
+    qbe_handle* h = b->sims[i];
+    const int Nx = h->g.Nx, N = h->g.N;
+    if (collide_post(h->tab, h->cw, h->Cb, Nx, h->stream, h->launches) != cudaSuccess ||
+        rk_stage1(h->W, h->Cb, h->B, dt, h->F0, h->Wa, Nx, N, h->stream, h->launches, nullptr) != cudaSuccess ||
+        collide_pre(h->tab, h->cw, h->Wa, Nx, h->stream, h->launches) != cudaSuccess)
+      r = QBE_ERR_CUDA;
+  }
+  join();
+  if (!r) r = i3_all(launches);
+  // second collision's assembly, RK stage 2, transport half step
+  fork();
+  for (size_t i = 0; i < ns && !r; ++i) {
+    qbe_handle* h = b->sims[i];
+    const int Nx = h->g.Nx, N = h->g.N;
+    if (collide_post(h->tab, h->cw, h->Cb, Nx, h->stream, h->launches) != cudaSuccess ||
+        rk_stage2(h->W, h->F0, h->Cb, h->Wa, h->B, dt, h->W, Nx, N, h->stream, h->launches, nullptr) !=
+            cudaSuccess)
+      r = QBE_ERR_CUDA;
+    if (!r) r = do_advect(h, 0.5 * dt);   // even number of state-buffer swaps over the step: ends in h->W
+  }
+  join();
+  for (size_t i = 0; i < ns; ++i) {
+    b->sims[i]->stream = saved[i];
+    b->sims[i]->timer.on = was_on[i];
+  }
+  return r;
+}
+
 }  // namespace
 
 extern "C" {
@@ -880,24 +985,7 @@ int qbe_batch_step(qbe_batch* b, double dt, int nsteps) {
     // the legacy default stream cannot be captured: capture on the first branch stream instead
     cudaStream_t origin = b->stream ? b->stream : b->side[0];
     if (e != cudaSuccess) return bfail(b, QBE_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
-    int r = QBE_OK;
-    cudaEventRecord(b->fork, origin);
-    for (size_t i = 0; i < b->sims.size() && r == QBE_OK; ++i) {
-      qbe_handle* h = b->sims[i];
-      cudaStream_t br = (origin == b->side[i]) ? origin : b->side[i];
-      if (br != origin) cudaStreamWaitEvent(br, b->fork, 0);
-      const cudaStream_t saved = h->stream;
-      const bool was_on = h->timer.on;
-      h->timer.on = false;
-      h->stream = br;
-      r = do_step(h, dt);                     // even number of state-buffer swaps: ends in h->W again
-      h->stream = saved;
-      h->timer.on = was_on;
-      if (br != origin) {
-        cudaEventRecord(b->join[i], br);
-        cudaStreamWaitEvent(origin, b->join[i], 0);
-      }
-    }
+    int r = batch_capture_step(b, dt, origin);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(origin, &g);
     if (r != QBE_OK || e != cudaSuccess) {
