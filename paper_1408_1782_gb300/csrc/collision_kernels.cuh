@@ -571,8 +571,8 @@ size_t i3_staged_smem_bytes() {
 
 template <int n, class T>
 void set_smem_attributes() {
-  static bool done = false;
-  if (done) return;
+  static unsigned long long done = 0;
+  if (!first_on_device(done)) return;
   const int sm = (int)smem_bytes<n, T>();
   cudaFuncSetAttribute(k_prep<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i1<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -581,7 +581,6 @@ void set_smem_attributes() {
   cudaFuncSetAttribute(k_assemble<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     cudaFuncSetAttribute(k_i3_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
-  done = true;
 }
 
 template <int n, class T>

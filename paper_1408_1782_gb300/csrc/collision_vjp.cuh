@@ -697,8 +697,8 @@ __global__ void __launch_bounds__(kThreads) k_vjp_final(
 
 template <int n, class T>
 void set_vjp_smem_attributes() {
-  static bool done = false;
-  if (done) return;
+  static unsigned long long done = 0;
+  if (!first_on_device(done)) return;
   const int sm = (int)smem_bytes<n, T>();
   cudaFuncSetAttribute(k_vjp_seed<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i1_vjp<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -707,7 +707,6 @@ void set_vjp_smem_attributes() {
   cudaFuncSetAttribute(k_vjp_final<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     cudaFuncSetAttribute(k_i3_vjp_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
-  done = true;
 }
 
 // Forward prep/I1/I2+I4 (the VJP needs wfine, D^, K2, K4^) then the transpose kernels.

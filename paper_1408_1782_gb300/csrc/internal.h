@@ -116,6 +116,17 @@ struct VjpWork {
 // Launch configuration helpers.
 constexpr int kThreads = 256;
 
+// Per-device once-flags (function attributes are set per device): true the first time for the
+// current device.
+inline bool first_on_device(unsigned long long& done_mask) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done_mask & bit) return false;
+  done_mask |= bit;
+  return true;
+}
+
 // Kernel groups for the per-kernel device-time accounting (qbe_kernel_time).
 enum KernelGroup { KG_PREP = 0, KG_I1 = 1, KG_I24 = 2, KG_I3 = 3, KG_ASSEMBLE = 4, KG_TRANSPORT = 5, KG_RK = 6,
                    KG_VJP = 7, KG_VJP_I3 = 8, KG_ADJ_TRANSPORT = 9, KG_COUNT = 10 };
