@@ -258,7 +258,8 @@ long long qbe_launch_count(const qbe_handle* h);
  * qbe_kernel_time() synchronises the stream and returns the accumulated
  * device time (ms) and launch count of one group since enabling.  Groups:
  * 0 coefficients/prep, 1 I1 (C_c), 2 I2+I4, 3 I3 (Hu-Ying term),
- * 4 assembly/projection, 5 transport, 6 RK/precession update. */
+ * 4 assembly/projection, 5 transport, 6 RK/precession update, 7-9 the
+ * adjoint's kernels (below). */
 #define QBE_KG_PREP 0
 #define QBE_KG_I1 1
 #define QBE_KG_I24 2
@@ -273,17 +274,21 @@ int qbe_enable_timing(qbe_handle* h, int enable);
 int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launches);
 
 /* ------------------------------------------------------------------------
- * Batches of independent simulations (SURVEY (f), batching form): several
- * solver handles -- any mix of N, Nx, J, M, precision, boundary conditions and
- * B fields, all on one device -- stepped together.  The first qbe_batch_step
- * with a given dt captures one split step (Sec. 4) of every simulation into a
- * CUDA graph, each simulation on its own branch so that independent
- * simulations run concurrently; every step is then one graph launch.
- * qbe_batch_autotune times, per simulation, the persistent grid (1..3 blocks
- * per SM) and the number of m-chunks per (cell, angle) unit of the I3 kernel
- * on the simulation's current state and keeps the fastest (it drops any
- * captured graph).  Results are those of qbe_step on each handle, up to the
- * summation order of the I3 partial sums that the tuned shape selects.
+ * Batches of independent simulations: several solver handles -- any mix of
+ * N, Nx, J, M, precision, boundary conditions and B fields, all on one
+ * device -- stepped together (the simulations are independent, Sec. 3.2).
+ * The first qbe_batch_step with a given dt captures one split step (Sec. 4)
+ * of every simulation into a CUDA graph; every step is then one graph launch.
+ * The graph runs, per simulation on its own branch, the transport and the
+ * per-cell collision terms, and between them one I3 (Hu-Ying term) launch per
+ * padded-grid size and precision whose work queue covers the (simulation,
+ * cell, angle, m-chunk) units of every simulation of that size.  Results
+ * equal those of qbe_step on each handle (the same kernels on the same units).
+ * qbe_batch_autotune times, per simulation, the number of m-chunks per (cell,
+ * angle) unit and the I3 grid of single-simulation evaluations on the
+ * simulation's current state and keeps the fastest (it drops any captured
+ * graph); a changed m-chunking regroups the I3 partial sums (results then
+ * differ from untuned steps by rounding).
  * The handles stay owned by the caller and must outlive the batch; each may
  * appear once.  With a stream set (qbe_batch_set_stream) the steps are
  * asynchronous on it; without one, qbe_batch_step synchronises before it
