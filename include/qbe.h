@@ -42,7 +42,7 @@ extern "C" {
 #define QBE_ERR_CUDA (-2)         /* a CUDA runtime call or kernel launch failed     */
 #define QBE_ERR_ALLOC (-3)        /* device or host allocation failed                */
 #define QBE_ERR_STATE (-4)        /* call out of order (e.g. step before set_state)  */
-#define QBE_ERR_UNSUPPORTED (-5)  /* valid in the paper, not supported by this build */
+#define QBE_ERR_UNSUPPORTED (-5)  /* valid in the paper, not supported by this library */
 
 /* Discretisation (Sec. 3.2, Sec. 5): N velocity points per dimension (Fourier
  * cut-off, N in {8, 16, 32, 48, 64, 96, 128}); Nx finite volumes; J angular points on
