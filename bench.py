@@ -140,7 +140,8 @@ def config_dict(wl, ngpu, reference=False):
                      f"{int(100 * wl['perturb'])}% perturbed synthetic W"),
         "N": wl["N"], "Nx": wl["Nx"], "J": wl["J"], "M": wl["M"], "dt": wl["dt"],
         "bc": wl["bc"], "B": list(wl["B"]), "precision": "f64" if wl.get("precision", 0) == 0 else "f32-split",
-        "l2": "256 MiB buffer zeroed before every timed step (working set also exceeds L2)",
+        "l2": ("not applicable (host cores)" if reference else
+               "256 MiB buffer zeroed before every timed step (working set also exceeds L2)"),
         "parallelism": "oracle on host cores" if reference else ("single GPU" if ngpu == 1 else f"{ngpu} replicas"),
     }
 

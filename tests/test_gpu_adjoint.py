@@ -336,3 +336,23 @@ def test_step_vjp_for_several_cotangents_in_one_sweep(qbe):
         a, b = s.step_vjp(lams[k].copy())
         assert np.array_equal(a, l0[k]) and np.array_equal(b, gb[k])
     s.close()
+
+
+def test_step_vjp_fp32_split_matches_fp64(qbe):
+    """The reverse sweep of the FP32-split form against the FP64 form (N = 16, J = M = 8, four steps with
+    a field and Maxwell walls): the FP32 collision products carry the FP32-split tolerance."""
+    N, Nx, J, M = 16, 5, 8, 8
+    W = inputs.synthetic_w(N, Nx, seed=98, perturb=0.05)
+    B = inputs.uniform_b(Nx, (0.2, -0.1, 0.4))
+    out = []
+    for prec in (0, 1):
+        s = gpu_solver(qbe, N, Nx, J, M, "maxwell", precision=prec)
+        s.set_state(W)
+        s.set_bfield(B)
+        s.step_checkpointed(0.005, 4, 2)
+        lam = s.observables_vjp(np.array([1.0, 0.5]))
+        out.append(s.step_vjp(lam))
+        s.close()
+    (l64, b64), (l32, b32) = out
+    assert np.abs(l32 - l64).max() < 5e-6 * np.abs(l64).max()
+    assert np.abs(b32 - b64).max() < 5e-6 * np.abs(b64).max()
