@@ -45,7 +45,7 @@ FP32_FMA_PER_CLK_PER_SM = 128        # measured 116 FFMA/clk/SM
 # DRAM bytes (read + write) per (cell, j, m) unit of the I3 kernel from one ncu capture of an 8-cell
 # slice of the current kernel (profiles/k_i3_f64_n64_8cells.md, profiles/k_i3_smem_f32_n64_8cells.md),
 # scaled by units; absent for sizes with no capture of the current kernel.
-I3_DRAM_BYTES_PER_UNIT = {(64, 0): 118.40e9 / 8192, (64, 1): 5.464e9 / 8192}
+I3_DRAM_BYTES_PER_UNIT = {(64, 0): 119.85e9 / 8192, (64, 1): 5.548e9 / 8192}
 
 
 def workload(name="plain_fp64_n64", precision=None):
