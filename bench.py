@@ -310,6 +310,33 @@ def run_ours(args):
     peak = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
     total_group_ms = sum(v["ms"] for v in groups.values())
 
+    # the streaming kernels (transport, RK/precession): algorithmic bytes and FP64 operations per
+    # launch over their live CUDA-event duration, against the measured copy bandwidth and the FP64
+    # issue rate (FP64_FMA_PER_CLK_PER_SM lanes per clock per SM): on this part an FP64 stream of a
+    # few operations per 8-byte word is bound by the FP64 pipe before HBM.
+    hbm_peak = 6778.0
+    try:
+        hbm_peak = float(json.load(open(MEASURED_PEAKS)).get("hbm_gbs", hbm_peak))
+    except Exception:
+        pass
+    fp64_ops_peak = SM_COUNT * FP64_FMA_PER_CLK_PER_SM * sm_max * 1e6
+    nvel = Nx * N * N
+    sb = nvel * 4 * 8
+    streaming = {}
+    # k_advect: per output value 3 differences, 1 subtraction, 2 FMAs; reads and writes the state once.
+    # k_rk1 / k_rk2 (one timing group, per-kernel averages): 16 and 20 FP64 operations per velocity;
+    # 16 and 20 words of traffic per velocity (k_rk1: W, C in, F0, W1 out; k_rk2: W, F0, C1, W1 in, W out).
+    for gname, label, bytes_per_launch, ops_per_launch in (
+            ("transport", "k_advect", 2 * sb, 6 * 4 * nvel),
+            ("rk", "k_rk1+k_rk2 (per kernel)", (16 + 20) / 2 * 8 * nvel, (16 + 20) / 2 * nvel)):
+        ms, cnt = groups[gname]["ms"], groups[gname]["launches"]
+        if cnt and ms > 0:
+            t_launch = ms / cnt * 1e-3
+            gbs = bytes_per_launch / t_launch / 1e9
+            streaming[label] = {"bytes_per_launch": bytes_per_launch, "fp64_ops_per_launch": ops_per_launch,
+                                "avg_launch_us": 1e6 * t_launch, "GB_s": gbs, "frac_of_hbm": gbs / hbm_peak,
+                                "frac_of_fp64_issue": ops_per_launch / t_launch / fp64_ops_peak}
+
     precision_report = None
     if prec == 1 and rank == 0:
         precision_report = fp32_split_report(wl, W0, local, qbe, torch, np)
@@ -340,6 +367,7 @@ def run_ours(args):
                                          f"flop x {sm_max:.0f} MHz (microbenchmark: DFMA 1.20 TFLOP/s, FFMA 73.1 "
                                          f"TFLOP/s at 2002 MHz)")},
             "kernel_share": {k: round(v["ms"] / total_group_ms, 4) for k, v in groups.items()},
+            "streaming_kernels": streaming,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "cell·k-pts/s", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes, "steps": e2e_steps},

@@ -6,13 +6,22 @@
 // every access is coalesced.
 #include "internal.h"
 
+#include <cstdlib>
+
 namespace qbe {
 
 namespace {
 
+// eq. minmod: a if |a| <= |b| and ab > 0; b if |b| < |a| and ab > 0; 0 otherwise.  Signs and
+// magnitudes are compared on the IEEE bit patterns (integer pipe) instead of FP64 products and
+// compares: for finite a, b the value is the same (a zero operand yields zero either way) except
+// where the FP64 product a*b would underflow to zero (|a b| < 5e-324), where this returns the
+// smaller operand instead of zero.
 __device__ __forceinline__ double minmod(double a, double b) {
-  // a if |a| <= |b| and ab > 0; b if |b| < |a| and ab > 0; 0 otherwise
-  return (a * b > 0.0) ? (fabs(a) <= fabs(b) ? a : b) : 0.0;
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  if ((ia ^ ib) < 0) return 0.0;                                   // opposite signs
+  const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+  return ma <= mb ? a : b;
 }
 
 // Outgoing number flux of the boundary cells (Maxwell walls):
@@ -49,8 +58,9 @@ struct Ghost {
 };
 
 // Value of component c at velocity (ix, iy) in cell jj (may be a ghost cell).
+// The sign of v_x = dv (ix - N/2) is that of ix - N/2.
 __device__ __forceinline__ double cell_value(const double* __restrict__ W, int jj, int c, int ix, int iy, int Nx,
-                                             int N, double vx, const Ghost& g) {
+                                             int N, const Ghost& g) {
   const size_t NN = (size_t)N * N;
   const size_t off = (size_t)c * NN + (size_t)ix * N + iy;
   if (jj >= 0 && jj < Nx) return W[(size_t)jj * 4 * NN + off];
@@ -60,7 +70,7 @@ __device__ __forceinline__ double cell_value(const double* __restrict__ W, int j
   }
   const bool left = jj < 0;
   const int b = left ? 0 : Nx - 1;
-  const bool incoming = left ? (vx > 0.0) : (vx < 0.0);
+  const bool incoming = left ? (ix > N / 2) : (ix < N / 2);
   if (!incoming) return W[(size_t)b * 4 * NN + off];          // outgoing or v_x = 0: copy of the boundary cell
   const double* phi = left ? g.phiL : g.phiR;
   if (g.kind == QBE_DIRICHLET) return phi[off];
@@ -72,30 +82,54 @@ __device__ __forceinline__ double cell_value(const double* __restrict__ W, int j
   return (1.0 - g.alpha) * spec + g.alpha * phi[off] * (fb / Z);
 }
 
+// Coefficients of eq. slopeLimiterStep in the upwind frame for a velocity with |v_x| = av:
+// c_g = 2 k |v_x| and c_l = k (1 - |nu|) |v_x|, k = tau / (2 dx), |nu| = tau |v_x| / dx, kt = tau / dx.
+__host__ __device__ __forceinline__ void advect_coefs(double av, double kt, double& cg, double& cl) {
+  cg = kt * av;
+  cl = 0.5 * kt * (1.0 - kt * av) * av;
+}
+
+// The table of both coefficients per velocity row, built on the host for each sub-step and passed
+// by value (__grid_constant__: read from the constant bank, one broadcast per warp for N >= 32).
+// The device does no FP64 division and no per-block table set-up: on this part FP64 arithmetic
+// issues at about two lanes per clock per SM, so it is the bound of the transport kernels.
+struct AdvectCoefs {
+  double cg[128], cl[128];     // N <= 128
+};
+
+AdvectCoefs make_advect_coefs(int N, double dv, double kt) {
+  AdvectCoefs t{};
+  for (int ix = 0; ix < N; ++ix) advect_coefs(dv * std::abs(ix - N / 2), kt, t.cg[ix], t.cl[ix]);
+  return t;
+}
+
+// One grid row per (cell j, component c) (blockIdx.y = 4 j + c); threads over the N*N velocities,
+// so the stencil cells and their ghost rules are uniform over a block and a warp shares v_x
+// (N >= 32).  With s = sgn v_x and the upwind-ordered stencil q_d = W(j + s (d - 2)), d = 0..3,
+// eq. slopeLimiterStep reduces to
+//   W_out = q2 - c_g (q2 - q1) + c_l (minmod(q2 - q1, q1 - q0) - minmod(q3 - q2, q2 - q1)),
+// c_g = 2 k |v_x|, c_l = k (1 - |nu|) |v_x|, k = tau / (2 dx), nu = tau v_x / dx: the Godunov term
+// and the limiter term (sgn nu - nu)/2 of the downwind slope vanish.  (v_x = 0 leaves W unchanged.)
+// The two coefficients per velocity row are computed once per block; what remains per output is
+// three differences, one subtraction and two FMAs in FP64, the limiter on the integer pipe.
 __global__ void __launch_bounds__(256) k_advect(const double* __restrict__ W, double* __restrict__ Wout, int Nx,
-                                                int N, double L, double tau, Ghost g) {
-  const size_t NN = (size_t)N * N;
-  const size_t total = (size_t)Nx * 4 * NN;
-  const double dv = 2.0 * L / N;
-  const double dx = 1.0 / Nx;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(t / (4 * NN));
-    const int c = (int)((t / NN) % 4);
-    const int ix = (int)((t % NN) / N);
-    const int iy = (int)(t % N);
-    const double vx = dv * (ix - N / 2);
-    double Wv[5];
-#pragma unroll
-    for (int d = 0; d < 5; ++d) Wv[d] = cell_value(W, j - 2 + d, c, ix, iy, Nx, N, vx, g);
-    const double Sm1 = minmod(Wv[2] - Wv[1], Wv[1] - Wv[0]);
-    const double S0 = minmod(Wv[3] - Wv[2], Wv[2] - Wv[1]);
-    const double Sp1 = minmod(Wv[4] - Wv[3], Wv[3] - Wv[2]);
-    const double nu = tau * vx / dx;
-    const double sg = (nu > 0.0) ? 1.0 : (nu < 0.0 ? -1.0 : 0.0);
-    const double lim = 0.5 * (sg - nu);
-    const double godunov = -vx * (Wv[3] - Wv[1]) + fabs(vx) * (Wv[3] - 2.0 * Wv[2] + Wv[1]);
-    const double limiter = lim * (-vx * (Sp1 - Sm1) + fabs(vx) * (Sp1 - 2.0 * S0 + Sm1));
-    Wout[t] = Wv[2] + (tau / (2.0 * dx)) * (godunov + limiter);
+                                                int N, const __grid_constant__ AdvectCoefs cf, Ghost g) {
+  const int NN = N * N;
+  const int j = blockIdx.y >> 2, c = blockIdx.y & 3;
+  double* out = Wout + (size_t)blockIdx.y * NN;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < NN; v += gridDim.x * blockDim.x) {
+    const int ix = v / N, iy = v - ix * N;
+    const int sgn = ix < N / 2 ? -1 : 1;
+    const double q0 = cell_value(W, j - 2 * sgn, c, ix, iy, Nx, N, g);
+    const double q1 = cell_value(W, j - sgn, c, ix, iy, Nx, N, g);
+    const double q2 = cell_value(W, j, c, ix, iy, Nx, N, g);
+    const double q3 = cell_value(W, j + sgn, c, ix, iy, Nx, N, g);
+    const double b = q2 - q1;
+    const double su = minmod(b, q1 - q0);
+    const double s0 = minmod(q3 - q2, b);
+    double r = fma(-cf.cg[ix], b, q2);
+    r = fma(cf.cl[ix], su - s0, r);
+    out[v] = r;
   }
 }
 
@@ -107,14 +141,14 @@ __device__ __forceinline__ void prec(const double* b, double w1, double w2, doub
 }
 
 // F0 = C + 2 (B x w).sigma;  W1 = W + dt F0
+// blockIdx.y = cell, threads over the velocities.
 __global__ void __launch_bounds__(256) k_rk1(const double* __restrict__ W, const double* __restrict__ C,
                                              const double* __restrict__ B, double dt, double* __restrict__ F0,
                                              double* __restrict__ W1, int Nx, int N) {
-  const size_t NN = (size_t)N * N;
-  const size_t total = (size_t)Nx * NN;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t cell = t / NN, v = t % NN;
-    const size_t base = cell * 4 * NN + v;
+  const int NN = N * N;
+  const int cell = blockIdx.y;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < NN; v += gridDim.x * blockDim.x) {
+    const size_t base = (size_t)cell * 4 * NN + v;
     const double w0 = W[base], w1 = W[base + NN], w2 = W[base + 2 * NN], w3 = W[base + 3 * NN];
     double p1, p2, p3;
     prec(B + 3 * cell, w1, w2, w3, p1, p2, p3);
@@ -129,11 +163,10 @@ __global__ void __launch_bounds__(256) k_rk1(const double* __restrict__ W, const
 __global__ void __launch_bounds__(256) k_rk2(const double* W, const double* __restrict__ F0,
                                              const double* __restrict__ C1, const double* __restrict__ W1,
                                              const double* __restrict__ B, double dt, double* Wout, int Nx, int N) {
-  const size_t NN = (size_t)N * N;
-  const size_t total = (size_t)Nx * NN;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t cell = t / NN, v = t % NN;
-    const size_t base = cell * 4 * NN + v;
+  const int NN = N * N;
+  const int cell = blockIdx.y;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < NN; v += gridDim.x * blockDim.x) {
+    const size_t base = (size_t)cell * 4 * NN + v;
     double p1, p2, p3;
     prec(B + 3 * cell, W1[base + NN], W1[base + 2 * NN], W1[base + 3 * NN], p1, p2, p3);
     const double g[4] = {C1[base], C1[base + NN] + p1, C1[base + 2 * NN] + p2, C1[base + 3 * NN] + p3};
@@ -172,94 +205,80 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ W, i
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint of the transport substep.  With the minmod branches frozen at the
-// forward state (a tie |a| = |b| takes a's branch, as in minmod above) the
-// update is linear in the five stencil values; advect_coefs returns
-// dWout(j)/dWv[d] for the output (j, c, ix, iy).  The input cotangent is
-// gathered over every output whose stencil reads the input, directly or
-// through a ghost cell: periodic wrap, the copied boundary cell (outgoing
-// velocities), the specular image (1 - alpha) W_b(-v_x, v_y) and the
-// diffusive part alpha W_FD(v) Fbar / Z with Fbar a linear functional of the
-// boundary cell's w0 (Sec. 2).
+// Adjoint of the transport substep.  In the upwind frame of k_advect (s = sgn v_x, cell index
+// m -> W(j + s m)) the update of output cell jo is
+//   W_out(jo) = (1 - c_g) W(jo) + c_g W(jo - s) + c_l (sig(jo - s) - sig(jo)),
+//   sig(m)    = minmod(W(m + s) - W(m), W(m) - W(m - s)),
+// so with the minmod branches frozen at the forward state it is linear in W, and the cotangent
+// of any cell i (interior or ghost) is
+//   lam_in(i) = (1 - c_g) lam(i) + c_g lam(i + s) + sum_{m in {i - s, i, i + s}} mu(m) dsig(m)/dW(i),
+//   mu(m)     = c_l (lam(m + s) - lam(m))        (lam = 0 outside the domain),
+// which reads five W and four lam values.  The branch convention is eq. minmod's in the x
+// order: zero unless ab > 0; a tie |a| = |b| takes the x-forward difference W(m + 1) - W(m),
+// i.e. the first argument for s > 0 and the second for s < 0.  The ghost cells' cotangents
+// reach the interior through the ghost rules (Sec. 2): periodic wrap, the copied boundary cell
+// (outgoing velocities), the specular image (1 - alpha) W_b(-v_x, v_y) and the diffusive part
+// alpha W_FD(v) Fbar / Z with Fbar a linear functional of the boundary cell's w0.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int minmod_branch(double a, double b) {   // 0: zero, 1: a, 2: b
-  return (a * b > 0.0) ? (fabs(a) <= fabs(b) ? 1 : 2) : 0;
+
+// Frozen branch of sig: 0 zero, 1 the first argument a, 2 the second b.  Signs and magnitudes
+// on the bit patterns; a zero operand gives the zero branch (as ab > 0 fails for it).
+__device__ __forceinline__ int minmod_branch(double a, double b, bool tie_a) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+  if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0;
+  return (ma < mb || (tie_a && ma == mb)) ? 1 : 2;
 }
 
-__device__ __forceinline__ void advect_coefs(const double* __restrict__ W, int j, int c, int ix, int iy, int Nx,
-                                             int N, double vx, double tau, double dx, const Ghost& g,
-                                             double coef[5]) {
-  double Wv[5];
-#pragma unroll
-  for (int d = 0; d < 5; ++d) Wv[d] = cell_value(W, j - 2 + d, c, ix, iy, Nx, N, vx, g);
-  const double nu = tau * vx / dx;
-  const double sg = (nu > 0.0) ? 1.0 : (nu < 0.0 ? -1.0 : 0.0);
-  const double lim = 0.5 * (sg - nu);
-  const double k = tau / (2.0 * dx);
-  const double av = fabs(vx);
-  coef[0] = 0.0;
-  coef[1] = k * (vx + av);
-  coef[2] = 1.0 - 2.0 * k * av;
-  coef[3] = k * (-vx + av);
-  coef[4] = 0.0;
-  const double cm = k * lim * (vx + av), c0 = k * lim * (-2.0 * av), cp = k * lim * (-vx + av);
-  // S_{-1} = minmod(W2 - W1, W1 - W0)
-  switch (minmod_branch(Wv[2] - Wv[1], Wv[1] - Wv[0])) {
-    case 1: coef[2] += cm; coef[1] -= cm; break;
-    case 2: coef[1] += cm; coef[0] -= cm; break;
-    default: break;
-  }
-  // S_0 = minmod(W3 - W2, W2 - W1)
-  switch (minmod_branch(Wv[3] - Wv[2], Wv[2] - Wv[1])) {
-    case 1: coef[3] += c0; coef[2] -= c0; break;
-    case 2: coef[2] += c0; coef[1] -= c0; break;
-    default: break;
-  }
-  // S_{+1} = minmod(W4 - W3, W3 - W2)
-  switch (minmod_branch(Wv[4] - Wv[3], Wv[3] - Wv[2])) {
-    case 1: coef[4] += cp; coef[3] -= cp; break;
-    case 2: coef[3] += cp; coef[2] -= cp; break;
-    default: break;
-  }
+__device__ __forceinline__ double lam_at(const double* __restrict__ lam, int jj, int Nx, size_t off, size_t NN4,
+                                         int kind) {
+  if (kind == QBE_PERIODIC) jj = (jj % Nx + Nx) % Nx;
+  else if (jj < 0 || jj >= Nx) return 0.0;
+  return lam[(size_t)jj * NN4 + off];
 }
 
-// Cotangent that reaches ghost cell gcell (outside [0, Nx)) at (c, ix, iy):
-// sum over outputs jo and stencil slots d with jo - 2 + d = gcell.
-__device__ __forceinline__ double ghost_cotangent(const double* __restrict__ W, const double* __restrict__ lam,
-                                                  int gcell, int c, int ix, int iy, int Nx, int N, double vx,
-                                                  double tau, double dx, const Ghost& g) {
+// Cotangent of cell i (any index, ghosts included) at (c, ix, iy), before the ghost rules.
+__device__ __forceinline__ double cell_cotangent(const double* __restrict__ W, const double* __restrict__ lam,
+                                                 int i, int c, int ix, int iy, int Nx, int N, double cg, double cl,
+                                                 const Ghost& g) {
+  const int s = ix < N / 2 ? -1 : 1;
   const size_t NN = (size_t)N * N;
   const size_t off = (size_t)c * NN + (size_t)ix * N + iy;
-  double acc = 0.0;
-  for (int d = 0; d < 5; ++d) {
-    const int jo = gcell + 2 - d;
-    if (jo < 0 || jo >= Nx) continue;
-    double coef[5];
-    advect_coefs(W, jo, c, ix, iy, Nx, N, vx, tau, dx, g, coef);
-    acc += lam[(size_t)jo * 4 * NN + off] * coef[d];
-  }
+  double w[5], l[4];          // w[e + 2] = W(i + s e), e = -2..2;  l[e + 1] = lam(i + s e), e = -1..2
+#pragma unroll
+  for (int e = 0; e < 5; ++e) w[e] = cell_value(W, i + s * (e - 2), c, ix, iy, Nx, N, g);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) l[e] = lam_at(lam, i + s * (e - 1), Nx, off, 4 * NN, g.kind);
+  const bool tie_a = s > 0;
+  double acc = fma(cg, l[2] - l[1], l[1]);
+  // sig(i - s): i is its W(m + s) (branch a: +mu)
+  if (minmod_branch(w[2] - w[1], w[1] - w[0], tie_a) == 1) acc = fma(cl, l[1] - l[0], acc);
+  // sig(i): i is its W(m) (branch a: -mu, branch b: +mu)
+  const int b0 = minmod_branch(w[3] - w[2], w[2] - w[1], tie_a);
+  if (b0 != 0) acc = fma(b0 == 1 ? -cl : cl, l[2] - l[1], acc);
+  // sig(i + s): i is its W(m - s) (branch b: -mu)
+  if (minmod_branch(w[4] - w[3], w[3] - w[2], tie_a) == 2) acc = fma(-cl, l[3] - l[2], acc);
   return acc;
 }
 
-// Maxwell walls: gsum[side] = sum over incoming velocities and components of
-// the ghost cotangents times W_FD (the diffusive part's dependence on Fbar).
+// Maxwell walls: gsum[side] = sum over incoming velocities and components of the two ghost
+// cells' cotangents times W_FD (the diffusive part's dependence on Fbar).
 __global__ void __launch_bounds__(256) k_wall_adj(const double* __restrict__ W, const double* __restrict__ lam,
-                                                  int Nx, int N, double L, double tau, Ghost g, double* gsum) {
+                                                  int Nx, int N, const __grid_constant__ AdvectCoefs cf, Ghost g,
+                                                  double* gsum) {
   __shared__ double red[256];
   const int side = blockIdx.x;
   const int NN = N * N;
-  const double dv = 2.0 * L / N;
-  const double dx = 1.0 / Nx;
   const double* phi = side == 0 ? g.phiL : g.phiR;
   double acc = 0.0;
   for (int t = threadIdx.x; t < 4 * NN; t += blockDim.x) {
     const int c = t / NN, ix = (t % NN) / N, iy = t % N;
-    const double vx = dv * (ix - N / 2);
-    const bool incoming = side == 0 ? (vx > 0.0) : (vx < 0.0);
+    const bool incoming = side == 0 ? (ix > N / 2) : (ix < N / 2);
     if (!incoming) continue;
+    const double cg = cf.cg[ix], cl = cf.cl[ix];
     const int g0 = side == 0 ? -2 : Nx, g1 = side == 0 ? -1 : Nx + 1;
-    const double lg = ghost_cotangent(W, lam, g0, c, ix, iy, Nx, N, vx, tau, dx, g) +
-                      ghost_cotangent(W, lam, g1, c, ix, iy, Nx, N, vx, tau, dx, g);
+    const double lg = cell_cotangent(W, lam, g0, c, ix, iy, Nx, N, cg, cl, g) +
+                      cell_cotangent(W, lam, g1, c, ix, iy, Nx, N, cg, cl, g);
     acc += lg * phi[t];
   }
   red[threadIdx.x] = acc;
@@ -271,58 +290,44 @@ __global__ void __launch_bounds__(256) k_wall_adj(const double* __restrict__ W, 
   if (threadIdx.x == 0) gsum[side] = red[0];
 }
 
+// Grid as k_advect: blockIdx.y = 4 j + c, threads over the velocities.
 __global__ void __launch_bounds__(256) k_advect_vjp(const double* __restrict__ W, const double* __restrict__ lam,
-                                                    double* __restrict__ lam_in, int Nx, int N, double L, double tau,
-                                                    Ghost g, const double* __restrict__ gsum) {
-  const size_t NN = (size_t)N * N;
-  const size_t total = (size_t)Nx * 4 * NN;
-  const double dv = 2.0 * L / N;
-  const double dx = 1.0 / Nx;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(t / (4 * NN));
-    const int c = (int)((t / NN) % 4);
-    const int ix = (int)((t % NN) / N);
-    const int iy = (int)(t % N);
-    const size_t off = (size_t)c * NN + (size_t)ix * N + iy;
-    const double vx = dv * (ix - N / 2);
-    double acc = 0.0;
-    for (int d = 0; d < 5; ++d) {
-      int jo = j + 2 - d;
-      if (g.kind == QBE_PERIODIC) {
-        jo = (jo % Nx + Nx) % Nx;
-      } else if (jo < 0 || jo >= Nx) {
-        continue;
-      }
-      double coef[5];
-      advect_coefs(W, jo, c, ix, iy, Nx, N, vx, tau, dx, g, coef);
-      acc += lam[(size_t)jo * 4 * NN + off] * coef[d];
-    }
+                                                    double* __restrict__ lam_in, int Nx, int N, double dv,
+                                                    const __grid_constant__ AdvectCoefs cf, Ghost g,
+                                                    const double* __restrict__ gsum) {
+  const int NN = N * N;
+  const int j = blockIdx.y >> 2, c = blockIdx.y & 3;
+  double* out = lam_in + (size_t)blockIdx.y * NN;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < NN; v += gridDim.x * blockDim.x) {
+    const int ix = v / N, iy = v - ix * N;
+    const double cg = cf.cg[ix], cl = cf.cl[ix];
+    double acc = cell_cotangent(W, lam, j, c, ix, iy, Nx, N, cg, cl, g);
     if (g.kind != QBE_PERIODIC) {
       for (int side = 0; side < 2; ++side) {
         if (j != (side == 0 ? 0 : Nx - 1)) continue;
         const int g0 = side == 0 ? -2 : Nx, g1 = side == 0 ? -1 : Nx + 1;
-        const bool incoming = side == 0 ? (vx > 0.0) : (vx < 0.0);
-        if (!incoming)   // the ghost copies this boundary value
-          acc += ghost_cotangent(W, lam, g0, c, ix, iy, Nx, N, vx, tau, dx, g) +
-                 ghost_cotangent(W, lam, g1, c, ix, iy, Nx, N, vx, tau, dx, g);
+        const bool incoming = side == 0 ? (ix > N / 2) : (ix < N / 2);
+        if (!incoming)   // both ghosts copy this boundary value
+          acc += cell_cotangent(W, lam, g0, c, ix, iy, Nx, N, cg, cl, g) +
+                 cell_cotangent(W, lam, g1, c, ix, iy, Nx, N, cg, cl, g);
         if (g.kind == QBE_MAXWELL) {
-          // specular image: this value feeds the ghost at velocity index N - ix when that one is incoming
+          // specular image: this value feeds the ghosts at velocity index N - ix (v_x -> -v_x) when those are
+          // incoming (|v_x| and so c_g, c_l are the same there)
           const int mx = N - ix;
-          const double vm = -vx;
-          const bool m_in = side == 0 ? (vm > 0.0) : (vm < 0.0);
+          const bool m_in = side == 0 ? (mx > N / 2) : (mx < N / 2);
           if (mx < N && m_in)
-            acc += (1.0 - g.alpha) * (ghost_cotangent(W, lam, g0, c, mx, iy, Nx, N, vm, tau, dx, g) +
-                                      ghost_cotangent(W, lam, g1, c, mx, iy, Nx, N, vm, tau, dx, g));
+            acc += (1.0 - g.alpha) * (cell_cotangent(W, lam, g0, c, mx, iy, Nx, N, cg, cl, g) +
+                                      cell_cotangent(W, lam, g1, c, mx, iy, Nx, N, cg, cl, g));
           // diffusive part through Fbar = dv^2 sum_{outgoing} 2 w0 |v_x|
-          const bool out = side == 0 ? (vx < 0.0) : (vx > 0.0);
-          if (c == 0 && out) {
+          const bool outg = side == 0 ? (ix < N / 2) : (ix > N / 2);
+          if (c == 0 && outg) {
             const double Z = side == 0 ? g.ZL : g.ZR;
-            acc += g.alpha / Z * dv * dv * 2.0 * fabs(vx) * gsum[side];
+            acc += g.alpha / Z * dv * dv * 2.0 * (dv * abs(ix - N / 2)) * gsum[side];
           }
         }
       }
     }
-    lam_in[t] = acc;
+    out[v] = acc;
   }
 }
 
@@ -444,6 +449,12 @@ __global__ void __launch_bounds__(256) k_observables_vjp(const double* __restric
   }
 }
 
+// Grid over (velocity blocks) x (rows): rows = cells (x4 components for per-component kernels).
+dim3 grid_rows(int NN, int rows) {
+  const int bx = (NN + 255) / 256;
+  return dim3(bx < 1 ? 1 : bx, rows);
+}
+
 int grid_for(size_t total) {
   size_t g = (total + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
@@ -460,8 +471,8 @@ cudaError_t advect_substep(const double* Win, double* Wout, int Nx, int N, doubl
     ++launches;
   }
   Ghost g{bc.kind, bc.alpha, bc.ZL, bc.ZR, bc.phiL, bc.phiR, bc.fbar};
-  const size_t total = (size_t)Nx * 4 * N * N;
-  k_advect<<<grid_for(total), 256, 0, s>>>(Win, Wout, Nx, N, L, tau, g);
+  const AdvectCoefs cf = make_advect_coefs(N, 2.0 * L / N, tau / (1.0 / Nx));
+  k_advect<<<grid_rows(N * N, Nx * 4), 256, 0, s>>>(Win, Wout, Nx, N, cf, g);
   if (tm) tm->end(s);
   ++launches;
   return cudaGetLastError();
@@ -470,7 +481,7 @@ cudaError_t advect_substep(const double* Win, double* Wout, int Nx, int N, doubl
 cudaError_t rk_stage1(const double* W, const double* C, const double* B, double dt, double* F0, double* W1,
                       int Nx, int N, cudaStream_t s, long long& launches, KernelTimer* tm) {
   if (tm) tm->begin(KG_RK, s);
-  k_rk1<<<grid_for((size_t)Nx * N * N), 256, 0, s>>>(W, C, B, dt, F0, W1, Nx, N);
+  k_rk1<<<grid_rows(N * N, Nx), 256, 0, s>>>(W, C, B, dt, F0, W1, Nx, N);
   if (tm) tm->end(s);
   ++launches;
   return cudaGetLastError();
@@ -479,7 +490,7 @@ cudaError_t rk_stage1(const double* W, const double* C, const double* B, double 
 cudaError_t rk_stage2(const double* W, const double* F0, const double* C1, const double* W1, const double* B,
                       double dt, double* Wout, int Nx, int N, cudaStream_t s, long long& launches, KernelTimer* tm) {
   if (tm) tm->begin(KG_RK, s);
-  k_rk2<<<grid_for((size_t)Nx * N * N), 256, 0, s>>>(W, F0, C1, W1, B, dt, Wout, Nx, N);
+  k_rk2<<<grid_rows(N * N, Nx), 256, 0, s>>>(W, F0, C1, W1, B, dt, Wout, Nx, N);
   if (tm) tm->end(s);
   ++launches;
   return cudaGetLastError();
@@ -501,12 +512,13 @@ cudaError_t advect_substep_vjp(const double* Win, const double* lam_out, double*
     ++launches;
   }
   Ghost g{bc.kind, bc.alpha, bc.ZL, bc.ZR, bc.phiL, bc.phiR, bc.fbar};
+  const double dv = 2.0 * L / N;
+  const AdvectCoefs cf = make_advect_coefs(N, dv, tau / (1.0 / Nx));
   if (bc.kind == QBE_MAXWELL) {
-    k_wall_adj<<<2, 256, 0, s>>>(Win, lam_out, Nx, N, L, tau, g, gsum);
+    k_wall_adj<<<2, 256, 0, s>>>(Win, lam_out, Nx, N, cf, g, gsum);
     ++launches;
   }
-  const size_t total = (size_t)Nx * 4 * N * N;
-  k_advect_vjp<<<grid_for(total), 256, 0, s>>>(Win, lam_out, lam_in, Nx, N, L, tau, g, gsum);
+  k_advect_vjp<<<grid_rows(N * N, Nx * 4), 256, 0, s>>>(Win, lam_out, lam_in, Nx, N, dv, cf, g, gsum);
   if (tm) tm->end(s);
   ++launches;
   return cudaGetLastError();

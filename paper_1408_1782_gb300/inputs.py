@@ -216,6 +216,16 @@ WORKLOADS = {
 }
 
 
+def minmod_tie_w(N: int, Nx: int, L: float = 12.0, seed: int = 0) -> np.ndarray:
+    """A state whose x-differences are exactly 0 or 1/64: one cell of synthetic_w rounded to
+    multiples of 1/64 and repeated over x, plus a ramp of 1/64 per cell on w0 where |v| < 4.
+    Every limiter argument pair with ab > 0 is then an exact tie |a| = |b| (away from walls)."""
+    W = np.repeat(np.round(synthetic_w(N, 1, L=L, seed=seed) * 64.0) / 64.0, Nx, axis=0)
+    vx, vy = velocity_mesh(N, L)
+    W[:, 0] += (np.arange(Nx)[:, None, None] / 64.0) * ((vx**2 + vy**2) < 16.0)
+    return W
+
+
 def random_field(shape, seed: int = 0, scale: float = 1.0) -> np.ndarray:
     """Seeded standard-normal field of the given shape (tangent directions and cotangents)."""
     rng = np.random.default_rng(seed)

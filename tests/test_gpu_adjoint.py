@@ -156,20 +156,26 @@ def gpu_solver(q, N, Nx, J, M, kind, precision=0, R=7.5):
     return s
 
 
+@pytest.mark.parametrize("N,Nx,J,M,nsteps,ties", [(8, 5, 4, 2, 3, False), (8, 5, 4, 2, 3, True),
+                                                   (64, 4, 2, 1, 1, True)])
 @pytest.mark.parametrize("kind", ["periodic", "dirichlet", "maxwell"])
-def test_step_vjp_transpose_identity(qbe, kind):
-    """Three split steps with two checkpoint segments (every = 2), B != 0, N = 8, Nx = 5.  R = 2 keeps
-    the explicit RK2 stable on this coarse grid (at R = 7.5, |C| ~ 26 and dt = 0.01 diverges)."""
-    N, Nx, J, M, R = 8, 5, 4, 2, 2.0
-    dt, nsteps = 0.01, 3
+def test_step_vjp_transpose_identity(qbe, pool, kind, N, Nx, J, M, nsteps, ties):
+    """Split steps with checkpoint segments of two steps, B != 0.  R = 2 keeps the explicit RK2
+    stable on the coarse N = 8 grid (at R = 7.5, |C| ~ 26 and dt = 0.01 diverges).  At N = 8 a warp
+    spans velocity rows of both signs of v_x; at N = 64 every warp is within one row.  With ties
+    the state's x-differences are exactly 0 or 1/64 (inputs.minmod_tie_w), so that every minmod
+    pair with ab > 0 away from the walls is a tie |a| = |b| in the first transport sub-step and the
+    tie convention of eq. minmod (a's branch) decides the derivative."""
+    R = 2.0
+    dt = 0.01
     p = O.Params(N=N, J=J, M=M, R=R)
     _, _, bc = boundary(kind)
-    W = inputs.synthetic_w(N, Nx, seed=50, perturb=0.05)
+    W = inputs.minmod_tie_w(N, Nx, seed=50) if ties else inputs.synthetic_w(N, Nx, seed=50, perturb=0.05)
     B = inputs.uniform_b(Nx, (0.3, -0.2, 0.5)) + inputs.random_field((Nx, 3), seed=51, scale=0.2)
     dW = inputs.random_field(W.shape, seed=52, scale=0.05)
     dB = inputs.random_field(B.shape, seed=53, scale=0.5)
     lam = inputs.random_field(W.shape, seed=54)
-    Wn, jv = T.evolve_jvp(W, B, dt, nsteps, p, bc, dW, dB)
+    Wn, jv = T.evolve_jvp(W, B, dt, nsteps, p, bc, dW, dB, mapper=pool)
     s = gpu_solver(qbe, N, Nx, J, M, kind, R=R)
     s.set_state(W)
     s.set_bfield(B)

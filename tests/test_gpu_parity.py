@@ -116,11 +116,13 @@ def test_collision_conserves_density_like_the_oracle(qbe):
     assert np.all(np.abs(rho).max(axis=1) < 1e-13 * scale)
 
 
+@pytest.mark.parametrize("N,Nx", [(8, 7), (64, 9)])
 @pytest.mark.parametrize("bc", ["periodic", "dirichlet", "maxwell"])
-def test_transport_matches_oracle(qbe, bc):
+def test_transport_matches_oracle(qbe, bc, N, Nx):
+    """N = 8: one partial block per (cell, component) row, warps spanning several v_x rows;
+    N = 64: 16 blocks per row, every warp within one v_x row."""
     import torch
 
-    N, Nx = 8, 7
     rng = np.random.default_rng(4)
     W = inputs.synthetic_w(N, Nx, seed=2) + 0.01 * rng.normal(size=(Nx, 4, N, N))
     fdL = (0.8, 1.5, -1.5, np.eye(2))
