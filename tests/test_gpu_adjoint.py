@@ -157,7 +157,7 @@ def gpu_solver(q, N, Nx, J, M, kind, precision=0, R=7.5):
 
 
 @pytest.mark.parametrize("N,Nx,J,M,nsteps,ties", [(8, 5, 4, 2, 3, False), (8, 5, 4, 2, 3, True),
-                                                   (64, 4, 2, 1, 1, True)])
+                                                   (8, 1, 4, 2, 2, False), (64, 4, 2, 1, 1, True)])
 @pytest.mark.parametrize("kind", ["periodic", "dirichlet", "maxwell"])
 def test_step_vjp_transpose_identity(qbe, pool, kind, N, Nx, J, M, nsteps, ties):
     """Split steps with checkpoint segments of two steps, B != 0.  R = 2 keeps the explicit RK2

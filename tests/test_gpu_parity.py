@@ -140,6 +140,48 @@ def test_transport_matches_oracle(qbe, bc, N, Nx):
     s.close()
 
 
+@pytest.mark.parametrize("N,Nx,bc,alpha", [
+    (8, 1, "periodic", 0.4), (8, 1, "dirichlet", 0.4), (8, 1, "maxwell", 0.0), (8, 1, "maxwell", 1.0),
+    (8, 2, "periodic", 0.4), (48, 3, "maxwell", 0.4), (128, 3, "maxwell", 0.7), (128, 2, "dirichlet", 0.4)])
+def test_transport_edge_cases_match_oracle(qbe, N, Nx, bc, alpha):
+    """One cell (both walls act on it, the periodic stencil wraps onto itself), two periodic cells,
+    pure specular (alpha = 0) and pure diffusive (alpha = 1) Maxwell walls, the radix-3 grid N = 48
+    and the largest grid N = 128."""
+    import torch
+
+    rng = np.random.default_rng(7)
+    W = inputs.synthetic_w(N, Nx, seed=9) + 0.01 * rng.normal(size=(Nx, 4, N, N))
+    fdL = (0.8, 1.5, -1.5, np.eye(2))
+    fdR = (1.2, 0.5, -0.5, np.array([[1, -1], [1, 1]]) / np.sqrt(2))
+    obc = O.Boundary(bc, fdL, fdR, alpha=alpha)
+    s = qbe.Solver(N, Nx, J=2, M=1, stream=torch.cuda.current_stream())
+    if bc != "periodic":
+        s.set_boundary(bc, qbe.fd_state(*fdL), qbe.fd_state(*fdR), alpha=alpha)
+    s.set_state(W)
+    tau = 1.7 / Nx / 12.0                    # |nu| = 1.7 -> two sub-steps
+    s.advect(tau)
+    got = s.get_state()
+    ref = O.advect(W, tau, O.Params(N=N), obc)
+    assert rel(got, ref) < TOL_ADV
+    s.close()
+
+
+def test_collision_largest_grid_fp64_matches_oracle(qbe):
+    """N = 128 (256 x 256 padded grid, the staged FP64 kernels), reduced quadrature J = M = 2."""
+    w = inputs.synthetic_w(128, 1, seed=13, perturb=0.05)
+    got = gpu_collide(qbe, w, 128, 2, 2)
+    ref = O.collision(w, O.Params(N=128, J=2, M=2))
+    assert rel(got, ref) < TOL_C
+
+
+def test_collision_rejects_an_empty_batch(qbe):
+    """ncells = 0 is an argument error of qbe_collide (QBE_ERR_ARG), not a silent no-op."""
+    s = qbe.Solver(8, 2, J=2, M=1)
+    with pytest.raises(qbe.QbeError):
+        s.collide(np.zeros((0, 4, 8, 8)))
+    s.close()
+
+
 def test_rk2_substep_with_field_matches_oracle(qbe):
     import torch
 
