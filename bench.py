@@ -694,6 +694,7 @@ def adjoint_cpu_baseline(wl):
 
 def run_vjp_only(args, wl, local):
     """Collision VJPs (dC/dW)^T lam of the first `cells` cells of the workload's initial state."""
+    import numpy as np
     import torch
 
     from paper_1408_1782_gb300 import inputs, qbe
@@ -705,25 +706,35 @@ def run_vjp_only(args, wl, local):
                    precision=wl.get("precision", 0))
     W = inputs.synthetic_w(N, wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])[:cells]
     w = torch.from_numpy(W.copy()).cuda()
-    lam = torch.from_numpy(inputs.random_field(W.shape, seed=1)).cuda()
-    g = torch.empty_like(w)
+    K = max(1, args.cotangents)
+    lam = torch.from_numpy(np.stack([inputs.random_field(W.shape, seed=1 + k) for k in range(K)])).cuda()
+    g = torch.empty_like(lam)
+
+    def product():
+        if K == 1:
+            s.collide_vjp(w, lam[0], out=g[0])
+        else:
+            s.collide_vjp_many(w, lam, out=g)
+
     for _ in range(args.warmup):
-        s.collide_vjp(w, lam, out=g)
+        product()
     torch.cuda.synchronize()
     s.enable_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        s.collide_vjp(w, lam, out=g)
+        product()
     e1.record(stream)
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
     v_ms, v_n = s.kernel_time("vjp_i3")
-    flops = cells * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N)
-    line = {"mode": "vjp", "metric": "dC/dW^T products, cell·k-pts/s", "value": args.steps * cells * N * N / (t_ms * 1e-3),
-            "unit": "cell·k-pts/s", "cells": cells, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_product": t_ms / args.steps, "vjp_i3_ms_per_launch": v_ms / max(v_n, 1),
-            "vjp_i3_tflops": flops / (v_ms / max(v_n, 1) * 1e-3) / 1e12,
+    # one I3 transpose launch carries all K products (up to four); work per product as for K = 1
+    flops = K * cells * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N)
+    line = {"mode": "vjp", "metric": "dC/dW^T products, cell·k-pts/s",
+            "value": K * args.steps * cells * N * N / (t_ms * 1e-3),
+            "unit": "cell·k-pts/s", "cells": cells, "cotangents": K, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_product": t_ms / args.steps / K, "vjp_i3_ms_per_launch": v_ms / max(v_n, 1),
+            "vjp_i3_tflops_per_product_convention": flops / (v_ms / max(v_n, 1) * 1e-3) / 1e12,
             "dtype": "f64" if wl.get("precision", 0) == 0 else "f32-split", "workload": wl["name"]}
     print(json.dumps(line), flush=True)
     s.close()
@@ -746,6 +757,8 @@ def main():
                     help="adjoint_n64: split steps per gradient (default: one checkpoint segment, 20)")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None)
     ap.add_argument("--cells", type=int, default=0)
+    ap.add_argument("--cotangents", type=int, default=1,
+                    help="--mode vjp: products per call at the same state (shared transforms, up to 4 per group)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -163,6 +163,18 @@ int qbe_moments(qbe_handle* h, double* rho, double* mom, double* energy, int on_
  * collision workspace).  Errors: QBE_ERR_ARG, QBE_ERR_ALLOC, QBE_ERR_CUDA. */
 int qbe_collide_vjp(qbe_handle* h, const double* w, const double* lam, double* grad, int ncells, int on_device);
 
+/* ncot products at the same state at once: grad[k] = (dC/dW at w)^T lam[k],
+ * k < ncot, with lam, grad [ncot][ncells][4][N][N] and w [ncells][4][N][N],
+ * all DEVICE memory (on_device must be 1).  The products are evaluated in
+ * groups that share the state's transforms (for the I3 term, the Psi'
+ * convolutions of the state: 8 of the 16 per (j, m) and product); groups
+ * are as in qbe_step_vjp_n;
+ * each result equals qbe_collide_vjp's bit for bit.  Grows the workspace to
+ * the group size on first use.  Errors: QBE_ERR_ARG (ncot < 1, ncells < 1,
+ * null pointers, on_device != 1), QBE_ERR_ALLOC, QBE_ERR_CUDA. */
+int qbe_collide_vjp_n(qbe_handle* h, int ncot, const double* w, const double* lam, double* grad, int ncells,
+                      int on_device);
+
 /* qbe_step(h, dt, nsteps) that also records a tape for qbe_step_vjp: the
  * state before every checkpoint_every-th step (ceil(nsteps/checkpoint_every)
  * states of device memory, kept by h and reused).  Any later call that
@@ -181,10 +193,17 @@ int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_e
 int qbe_step_vjp(qbe_handle* h, const double* lam_final, double* lam_init, double* grad_B, int on_device);
 
 /* The same reverse sweep for ncot cotangents at once (e.g. the gradients of
- * several observables): each segment is recomputed once and every cotangent
- * is swept over its intermediate states.  lam_final, lam_init [ncot][Nx][4][N][N],
+ * several observables): each segment is recomputed once and the cotangents
+ * are swept over its intermediate states in groups; within a group each
+ * collision product (dC/dW)^T is evaluated for all members at once, sharing
+ * the state's transforms (the I3 term's Psi' convolutions of the state, half
+ * of the transpose's work).  Groups hold up to four cotangents, one in the
+ * FP32-split form on padded grids up to 128 points, whose transpose keeps its
+ * transforms in shared memory and is bound by its per-cotangent global
+ * accumulators instead.  lam_final, lam_init [ncot][Nx][4][N][N],
  * grad_B [ncot][Nx][3] (may be NULL).  Results equal ncot calls of
- * qbe_step_vjp.  Extra memory: two states per cotangent. */
+ * qbe_step_vjp bit for bit.  Extra memory: two states per cotangent, and the
+ * collision product's cotangent buffers once per group member. */
 int qbe_step_vjp_n(qbe_handle* h, int ncot, const double* lam_final, double* lam_init, double* grad_B,
                    int on_device);
 

@@ -166,11 +166,11 @@ cudaError_t i3_group(const Tables* const* tabs, const CollisionWork* const* cws,
   return cudaErrorInvalidValue;
 }
 
-cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
-                        double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,
+cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* const* lam,
+                        double* const* grad, int K, int ncells, int accumulate, cudaStream_t s, long long& launches,
                         KernelTimer* tm) {
-  if (ncells > cw.nb || ncells > vw.nb || cw.prec != vw.prec) return cudaErrorInvalidValue;
-#define QBE_VJP_CALL(n, T) collide_vjp_n<n, T>(t, cw, vw, w, lam, grad, ncells, accumulate, s, launches, tm)
+  if (ncells > cw.nb || ncells > vw.nb || cw.prec != vw.prec || K < 1 || K > vw.kcap) return cudaErrorInvalidValue;
+#define QBE_VJP_CALL(n, T) collide_vjp_n<n, T>(t, cw, vw, w, lam, grad, K, ncells, accumulate, s, launches, tm)
   if (vw.prec == 1) {
     QBE_VJP_SWITCH(float, QBE_VJP_CALL)
   } else {
@@ -180,15 +180,26 @@ cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const d
   return cudaErrorInvalidValue;
 }
 
-cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec) {
+// Cotangents one collision product should carry.  The staged transpose kernels (FP64, and FP32 on
+// grids above 128 points) are bound by their transforms, so sharing the state's Psi' convolutions saves
+// about a quarter of the work per product at two cotangents (measured: FP64, N = 64, 16 cells, 847 ms
+// per single launch against 1297 ms for two).  The FP32 shared-memory kernel runs its transforms on chip
+// and is bound by its global accumulators; every further cotangent adds three fields of them per block,
+// which pushes the working set out of L2 (two cotangents: 685 ms against 2 x 333 ms, L2 hit rate 85 %
+// -> 68 %), so it takes one cotangent at a time.
+int vjp_cotangent_group(const Tables& t, int prec) { return (prec == 1 && t.n <= 128) ? 1 : kMaxCotangents; }
+
+cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec, int kcap) {
   const size_t P = (size_t)t.n * t.n;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int bps = vjp_bps(t, prec);
   if (bps < 1) return cudaErrorInvalidValue;
+  if (kcap < 1 || kcap > kMaxCotangents) return cudaErrorInvalidValue;
   vw.prec = prec;
   vw.nb = nb;
+  vw.kcap = kcap;
   vw.grid = nsm * bps;
   // about 4 waves of (cell, j, m-chunk) units
   int nmc = (4 * vw.grid + nb * t.J - 1) / (nb * t.J);
@@ -197,21 +208,23 @@ cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec) {
   vw.mch = (t.M + nmc - 1) / nmc;
   vw.nmc = (t.M + vw.mch - 1) / vw.mch;
   const size_t nparts = (size_t)nb * t.J * vw.nmc;
+  // per-cell kernels: 7 fields per cell; I3 transpose: 7 + 2 K fields per block (staged form)
   size_t ws_fields = 7 * (size_t)nb;
-  if (9 * (size_t)vw.grid > ws_fields) ws_fields = 9 * (size_t)vw.grid;
+  if ((7 + 2 * (size_t)kcap) * vw.grid > ws_fields) ws_fields = (7 + 2 * (size_t)kcap) * vw.grid;
+  const size_t kc = (size_t)kcap;
   const size_t cz = prec == 1 ? sizeof(float2) : sizeof(double2);
   const size_t rz = cz / 2;
   cudaError_t e;
 #define QBE_ALLOC(ptr, bytes) \
   if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) { free_vjp_work(vw); return e; }
-  QBE_ALLOC(vw.nu, (size_t)nb * 2 * P * cz);
-  QBE_ALLOC(vw.nuf, (size_t)nb * P * rz);
-  QBE_ALLOC(vw.muD, (size_t)nb * 2 * P * cz);
-  QBE_ALLOC(vw.muK2, (size_t)nb * P * rz);
-  QBE_ALLOC(vw.mu4, (size_t)nb * 2 * P * cz);
-  QBE_ALLOC(vw.mu3, (size_t)nb * 2 * P * cz);
-  QBE_ALLOC(vw.part_r, nparts * 2 * P * cz);
-  QBE_ALLOC(vw.part_s, nparts * 2 * P * cz);
+  QBE_ALLOC(vw.nu, kc * nb * 2 * P * cz);
+  QBE_ALLOC(vw.nuf, kc * nb * P * rz);
+  QBE_ALLOC(vw.muD, kc * nb * 2 * P * cz);
+  QBE_ALLOC(vw.muK2, kc * nb * P * rz);
+  QBE_ALLOC(vw.mu4, kc * nb * 2 * P * cz);
+  QBE_ALLOC(vw.mu3, kc * nb * 2 * P * cz);
+  QBE_ALLOC(vw.part_r, kc * nparts * 2 * P * cz);
+  QBE_ALLOC(vw.part_s, kc * nparts * 2 * P * cz);
   QBE_ALLOC(vw.ws, ws_fields * P * cz);
 #undef QBE_ALLOC
   return cudaSuccess;

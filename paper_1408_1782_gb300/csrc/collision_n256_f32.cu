@@ -5,8 +5,9 @@ namespace qbe {
 template cudaError_t collide_batch_n<256, float>(const Tables&, CollisionWork&, const double*, double*, int,
                                               cudaStream_t, long long&, KernelTimer*);
 template int i3_blocks_per_sm<256, float>();
-template cudaError_t collide_vjp_n<256, float>(const Tables&, CollisionWork&, VjpWork&, const double*, const double*,
-                                            double*, int, int, cudaStream_t, long long&, KernelTimer*);
+template cudaError_t collide_vjp_n<256, float>(const Tables&, CollisionWork&, VjpWork&, const double*,
+                                              const double* const*, double* const*, int, int, int, cudaStream_t,
+                                              long long&, KernelTimer*);
 template int i3_vjp_blocks_per_sm<256, float>();
 template cudaError_t collide_pre_n<256, float>(const Tables&, CollisionWork&, const double*, int, cudaStream_t,
                                             long long&, KernelTimer*);

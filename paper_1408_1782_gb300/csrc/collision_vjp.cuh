@@ -321,6 +321,21 @@ __global__ void __launch_bounds__(kThreads) k_i24_vjp(
   }
 }
 
+// dst = Psi'_j(x) for the field x(i) = ld(i), i = ix * n + iy: row FFT, column convolution with the
+// angle's psi' table, row IFFT (the forward's convolution); G is the staging field.
+template <int n, class C2, class T, class LD>
+__device__ __forceinline__ void psi_conv(C2* sm, const C2* tw, const T* __restrict__ psp, C2* G, LD ld, C2* dst) {
+  row_pass<n, -1, false, 0>(
+      sm, tw, [&](int ix, int iy) { return ld(ix * n + iy); }, NoMid(),
+      [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+  col_conv_pass<n>(
+      sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, [&](int ix, int iy) { return psp[ix * n + iy]; },
+      [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+  row_pass<n, 1, false, 0>(
+      sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+      [&](int ix, int iy, C2 v) { dst[ix * n + iy] = v; });
+}
+
 // --------------------------------------------------------------------------
 // I3 transpose (Hu-Ying term).  K3raw_b = sum_{j,m} sum_a eta_a S(w_a) T_ab,
 // T_ab = Psi'(w_a S(w_b)), with cotangents mu_b of K3raw_b:
@@ -331,6 +346,10 @@ __global__ void __launch_bounds__(kThreads) k_i24_vjp(
 // space with the conjugate phase; (ii) is accumulated in real space.
 // Persistent blocks over units (cell, j, m-chunk); per unit outputs a real
 // partial [2][P] and a spectral partial [2][P].
+// Several cotangents (K of them, mu3 / part_r / part_s of cotangent k at
+// offsets k * mu_stride and k * part_stride) share the shifted fields and the
+// T transforms, which depend on the state only: per (j, m) 8 + 8 K
+// convolutions instead of 16 K.
 // --------------------------------------------------------------------------
 template <int n, class T>
 __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
@@ -338,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
     const typename Vec2Of<T>::type* mu3, typename Vec2Of<T>::type* part_r, typename Vec2Of<T>::type* part_s,
     typename Vec2Of<T>::type* ws, const typename Vec2Of<T>::type* __restrict__ gtw,
     const T* __restrict__ psip_s, const typename Vec2Of<T>::type* __restrict__ phase, int J, int M, int nmc, int mch,
-    int nunits) {
+    int nunits, int K, size_t mu_stride, size_t part_stride) {
   using C2 = typename Vec2Of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
@@ -356,23 +375,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
   }
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
-  C2* slot = ws + (size_t)blockIdx.x * 9 * P;
+  C2* slot = ws + (size_t)blockIdx.x * (7 + 2 * K) * P;
   C2* Sig = slot;            // [2] shifted pairs
   C2* Tp = slot + 2 * P;     // [2] T_{a, pair}
   C2* Qp = slot + 4 * P;     // [2] Q_{a, pair}
-  C2* XZ = slot + 6 * P;     // [2] (i)+(iii) real-space terms, pairs by component
-  C2* G = slot + 8 * P;
+  C2* G = slot + 6 * P;
+  C2* XZall = slot + 7 * P;  // [K][2] (i)+(iii) real-space terms, pairs by component
   for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
     const int c = unit / (J * nmc);
     const int j = (unit / nmc) % J;
     const int mc = unit % nmc;
-    C2* accr = part_r + (size_t)unit * 2 * P;
-    C2* accs = part_s + (size_t)unit * 2 * P;
-    zero_fields(accr, 2 * P);
-    zero_fields(accs, 2 * P);
+    for (int k = 0; k < K; ++k) {
+      zero_fields(part_r + k * part_stride + (size_t)unit * 2 * P, 2 * P);
+      zero_fields(part_s + k * part_stride + (size_t)unit * 2 * P, 2 * P);
+    }
     const T* psp = psip_s + (size_t)j * P;
     const C2* wf = wfine + (size_t)c * 2 * P;
-    const C2* mu = mu3 + (size_t)c * 2 * P;
     const int m0 = mc * mch, m1 = min(M, m0 + mch);
     for (int m = m0; m < m1; ++m) {
       const C2* px = phase + ((size_t)j * M + m) * 2 * n;
@@ -388,81 +406,81 @@ __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
             sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : zero2<T>(); }, NoMid(),
             [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
       }
-      zero_fields(XZ, 2 * P);
+      zero_fields(XZall, 2 * K * P);
       for (int a = 0; a < 4; ++a) {
         const C2* wa = wf + (size_t)(a >> 1) * P;
         const C2* Sa = Sig + (size_t)(a >> 1) * P;
         const bool im = (a & 1) != 0;
         const T eta_a = (a == 0) ? (T)1 : (T)-1;
+        // T_{a, pair} = Psi'(w_a S_pair): the state's, shared by every cotangent
         for (int p = 0; p < 2; ++p) {
           const C2* Sp = Sig + (size_t)p * P;
-          const C2* mup = mu + (size_t)p * P;
-          for (int which = 0; which < 2; ++which) {   // 0: T = Psi'(w_a S_pair); 1: Q = Psi'(S_a mu_pair)
-            C2* dst = (which == 0 ? Tp : Qp) + (size_t)p * P;
-            row_pass<n, -1, false, 0>(
-                sm, tw,
-                [&](int ix, int iy) {
-                  const int i = ix * n + iy;
-                  if (which == 0) {
-                    const C2 z = wa[i];
-                    return cscale(Sp[i], im ? z.y : z.x);
-                  }
-                  const C2 s = Sa[i];
-                  return cscale(mup[i], im ? s.y : s.x);
-                },
-                NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
-            col_conv_pass<n>(
-                sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
-                [&](int ix, int iy) { return psp[ix * n + iy]; },
-                [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
-            row_pass<n, 1, false, 0>(
-                sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
-                [&](int ix, int iy, C2 v) { dst[ix * n + iy] = v; });
-          }
+          psi_conv<n>(sm, tw, psp, G,
+                      [&](int i) {
+                        const C2 z = wa[i];
+                        return cscale(Sp[i], im ? z.y : z.x);
+                      },
+                      Tp + (size_t)p * P);
         }
-        // pointwise: (i) X_a = eta_a sum_b mu_b T_ab ; (ii) Y_a = eta_a sum_b Q_ab S_b ; (iii) Z_b += eta_a w_a Q_ab
-        C2* accr_a = accr + (size_t)(a >> 1) * P;
-        C2* XZ_a = XZ + (size_t)(a >> 1) * P;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) {
-          const C2 t0 = Tp[i], t1 = Tp[P + i], q0 = Qp[i], q1 = Qp[P + i];
-          const C2 m0v = mu[i], m1v = mu[P + i];
-          const C2 s0 = Sig[i], s1 = Sig[P + i];
-          const C2 wz = wa[i];
-          const T wv = im ? wz.y : wz.x;
-          const T X = eta_a * (m0v.x * t0.x + m0v.y * t0.y + m1v.x * t1.x + m1v.y * t1.y);
-          const T Y = eta_a * (q0.x * s0.x + q0.y * s0.y + q1.x * s1.x + q1.y * s1.y);
-          if (im) {
-            accr_a[i].y += Y;
-            XZ_a[i].y += X;
-          } else {
-            accr_a[i].x += Y;
-            XZ_a[i].x += X;
+        for (int k = 0; k < K; ++k) {
+          const C2* mu = mu3 + k * mu_stride + (size_t)c * 2 * P;
+          C2* XZ = XZall + (size_t)k * 2 * P;
+          // Q_{a, pair} = Psi'(S_a mu_pair)
+          for (int p = 0; p < 2; ++p) {
+            const C2* mup = mu + (size_t)p * P;
+            psi_conv<n>(sm, tw, psp, G,
+                        [&](int i) {
+                          const C2 sv = Sa[i];
+                          return cscale(mup[i], im ? sv.y : sv.x);
+                        },
+                        Qp + (size_t)p * P);
           }
-          const T e = eta_a * wv;
-          XZ[i].x += e * q0.x;
-          XZ[i].y += e * q0.y;
-          XZ[P + i].x += e * q1.x;
-          XZ[P + i].y += e * q1.y;
+          // pointwise: (i) X_a = eta_a sum_b mu_b T_ab ; (ii) Y_a = eta_a sum_b Q_ab S_b ; (iii) Z_b += eta_a w_a Q_ab
+          C2* accr_a = part_r + k * part_stride + (size_t)unit * 2 * P + (size_t)(a >> 1) * P;
+          C2* XZ_a = XZ + (size_t)(a >> 1) * P;
+          for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const C2 t0 = Tp[i], t1 = Tp[P + i], q0 = Qp[i], q1 = Qp[P + i];
+            const C2 m0v = mu[i], m1v = mu[P + i];
+            const C2 s0 = Sig[i], s1 = Sig[P + i];
+            const C2 wz = wa[i];
+            const T wv = im ? wz.y : wz.x;
+            const T X = eta_a * (m0v.x * t0.x + m0v.y * t0.y + m1v.x * t1.x + m1v.y * t1.y);
+            const T Y = eta_a * (q0.x * s0.x + q0.y * s0.y + q1.x * s1.x + q1.y * s1.y);
+            if (im) {
+              accr_a[i].y += Y;
+              XZ_a[i].y += X;
+            } else {
+              accr_a[i].x += Y;
+              XZ_a[i].x += X;
+            }
+            const T e = eta_a * wv;
+            XZ[i].x += e * q0.x;
+            XZ[i].y += e * q0.y;
+            XZ[P + i].x += e * q1.x;
+            XZ[P + i].y += e * q1.y;
+          }
+          __syncthreads();
         }
-        __syncthreads();
       }
       // S^T: forward FFT of the XZ pairs, times the conjugate phase, accumulate in Fourier space
-      for (int p = 0; p < 2; ++p) {
-        const C2* src = XZ + (size_t)p * P;
-        C2* dst = accs + (size_t)p * P;
-        row_pass<n, -1, false, 0>(
-            sm, tw, [&](int ix, int iy) { return src[ix * n + iy]; }, NoMid(),
-            [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
-        col_pass<n, -1, false, 0>(
-            sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
-            [&](int ix, int iy, C2 v) {
-              const C2 ph = cmul(px[ix], py[iy]);
-              const C2 z = cmulc(v, ph);
-              C2 d = dst[ix * n + iy];
-              d.x += z.x;
-              d.y += z.y;
-              dst[ix * n + iy] = d;
-            });
+      for (int k = 0; k < K; ++k) {
+        for (int p = 0; p < 2; ++p) {
+          const C2* src = XZall + (size_t)(2 * k + p) * P;
+          C2* dst = part_s + k * part_stride + (size_t)unit * 2 * P + (size_t)p * P;
+          row_pass<n, -1, false, 0>(
+              sm, tw, [&](int ix, int iy) { return src[ix * n + iy]; }, NoMid(),
+              [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
+          col_pass<n, -1, false, 0>(
+              sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+              [&](int ix, int iy, C2 v) {
+                const C2 ph = cmul(px[ix], py[iy]);
+                const C2 z = cmulc(v, ph);
+                C2 d = dst[ix * n + iy];
+                d.x += z.x;
+                d.y += z.y;
+                dst[ix * n + iy] = d;
+              });
+        }
       }
     }
   }
@@ -481,7 +499,7 @@ template <int n>
 __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
     const float2* what, const float2* wfine, const float2* mu3, float2* part_r, float2* part_s, float2* ws,
     const float2* __restrict__ gtw, const float* __restrict__ psip_s, const float2* __restrict__ phase, int J, int M,
-    int nmc, int mch, int nunits) {
+    int nmc, int mch, int nunits, int K, size_t mu_stride, size_t part_stride) {
   using C2 = float2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
@@ -495,17 +513,17 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
     xmask[pos] = ((k < n / 4) || (k >= n - n / 4)) ? 1 : 0;
   }
   load_twiddles<n>(tw, gtw);
-  C2* slot = ws + (size_t)blockIdx.x * 9 * P;
+  C2* slot = ws + (size_t)blockIdx.x * (2 + 2 * K) * P;
   C2* Sig = slot;            // [2]
-  C2* XZ = slot + 2 * P;     // [2]
+  C2* XZall = slot + 2 * P;  // [K][2]
   for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
     const int c = unit / (J * nmc);
     const int j = (unit / nmc) % J;
     const int mc = unit % nmc;
-    C2* accr = part_r + (size_t)unit * 2 * P;
-    C2* accs = part_s + (size_t)unit * 2 * P;
-    zero_fields(accr, 2 * P);
-    zero_fields(accs, 2 * P);
+    for (int k = 0; k < K; ++k) {
+      zero_fields(part_r + k * part_stride + (size_t)unit * 2 * P, 2 * P);
+      zero_fields(part_s + k * part_stride + (size_t)unit * 2 * P, 2 * P);
+    }
     {
       const float4* src = reinterpret_cast<const float4*>(psip_s + (size_t)j * P);
       float4* dst = reinterpret_cast<float4*>(psm);
@@ -513,7 +531,6 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
       __syncthreads();
     }
     const C2* wf = wfine + (size_t)c * 2 * P;
-    const C2* mu = mu3 + (size_t)c * 2 * P;
     const int m0 = mc * mch, m1 = min(M, m0 + mch);
     for (int m = m0; m < m1; ++m) {
       const C2* px = phase + ((size_t)j * M + m) * 2 * n;
@@ -531,20 +548,19 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
         for (int idx = threadIdx.x; idx < P; idx += blockDim.x) S[idx] = G[(idx / n) * LS + idx % n];
         __syncthreads();
       }
-      zero_fields(XZ, 2 * P);
+      zero_fields(XZall, 2 * K * P);
       for (int a = 0; a < 4; ++a) {
         const C2* wa = wf + (size_t)(a >> 1) * P;
         const C2* Sa = Sig + (size_t)(a >> 1) * P;
-        C2* XZa = XZ + (size_t)(a >> 1) * P;
-        C2* accra = accr + (size_t)(a >> 1) * P;
         const bool im = (a & 1) != 0;
         const float eta_a = (a == 0) ? 1.f : -1.f;
         for (int p = 0; p < 2; ++p) {
           const C2* Sp = Sig + (size_t)p * P;
-          const C2* mup = mu + (size_t)p * P;
-          C2* XZp = XZ + (size_t)p * P;
-          for (int which = 0; which < 2; ++which) {
-            const C2* __restrict__ src = which == 0 ? Sp : mup;
+          // which 0: T = Psi'(w_a S_pair), the state's, shared by every cotangent;
+          // which 1: Q = Psi'(S_a mu_pair), once per cotangent
+          for (int which = 0; which < 1 + K; ++which) {
+            const int kq = which - 1;                          // cotangent of a Q transform
+            const C2* __restrict__ src = which == 0 ? Sp : mu3 + kq * mu_stride + (size_t)c * 2 * P + (size_t)p * P;
             const C2* __restrict__ scl = which == 0 ? wa : Sa;
 #pragma unroll 8
             for (int k = 0; k < kIter; ++k) {
@@ -559,22 +575,28 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
             fft_conv_lines<n>(G, n, 1, LS, tw, [&](int l, int pos) { return psm[pos * n + l]; });
             fft_lines<n, 1>(G, n, LS, 1, tw);
             if (which == 0) {
-              const C2* __restrict__ mv_ = mup;
-              float* __restrict__ xz = reinterpret_cast<float*>(XZa) + (im ? 1 : 0);
+              // (i): X_a += eta_a mu_pair . T for every cotangent
+              for (int kc = 0; kc < K; ++kc) {
+                const C2* __restrict__ mv_ = mu3 + kc * mu_stride + (size_t)c * 2 * P + (size_t)p * P;
+                float* __restrict__ xz =
+                    reinterpret_cast<float*>(XZall + (size_t)(2 * kc + (a >> 1)) * P) + (im ? 1 : 0);
 #pragma unroll 8
-              for (int k = 0; k < kIter; ++k) {
-                const int idx = threadIdx.x + k * kThreadsI3Smem;
-                if (kIter * kThreadsI3Smem == P || idx < P) {
-                  const C2 g = G[(idx / n) * LS + idx % n];
-                  const C2 mv = mv_[idx];
-                  xz[2 * idx] += eta_a * (mv.x * g.x + mv.y * g.y);
+                for (int k = 0; k < kIter; ++k) {
+                  const int idx = threadIdx.x + k * kThreadsI3Smem;
+                  if (kIter * kThreadsI3Smem == P || idx < P) {
+                    const C2 g = G[(idx / n) * LS + idx % n];
+                    const C2 mv = mv_[idx];
+                    xz[2 * idx] += eta_a * (mv.x * g.x + mv.y * g.y);
+                  }
                 }
               }
             } else {
+              // (ii) into the real-space partial, (iii) into Z_pair
               const C2* __restrict__ sp_ = Sp;
               const C2* __restrict__ wa_ = wa;
-              float* __restrict__ ar = reinterpret_cast<float*>(accra) + (im ? 1 : 0);
-              C2* __restrict__ xzp = XZp;
+              float* __restrict__ ar = reinterpret_cast<float*>(part_r + kq * part_stride + (size_t)unit * 2 * P +
+                                                                (size_t)(a >> 1) * P) + (im ? 1 : 0);
+              C2* __restrict__ xzp = XZall + (size_t)(2 * kq + p) * P;
 #pragma unroll 4
               for (int k = 0; k < kIter; ++k) {
                 const int idx = threadIdx.x + k * kThreadsI3Smem;
@@ -595,22 +617,24 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
           }
         }
       }
-      for (int p = 0; p < 2; ++p) {
-        const C2* src = XZ + (size_t)p * P;
-        C2* dst = accs + (size_t)p * P;
-        for (int idx = threadIdx.x; idx < P; idx += blockDim.x) G[(idx / n) * LS + idx % n] = src[idx];
-        __syncthreads();
-        fft_lines<n, -1>(G, n, LS, 1, tw);    // rows
-        fft_lines<n, -1>(G, n, 1, LS, tw);    // columns
-        for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
-          const int ix = idx / n, iy = idx % n;
-          const C2 z = cmulc(G[ix * LS + iy], cmul(px[ix], py[iy]));
-          C2 d = dst[idx];
-          d.x += z.x;
-          d.y += z.y;
-          dst[idx] = d;
+      for (int kc = 0; kc < K; ++kc) {
+        for (int p = 0; p < 2; ++p) {
+          const C2* src = XZall + (size_t)(2 * kc + p) * P;
+          C2* dst = part_s + kc * part_stride + (size_t)unit * 2 * P + (size_t)p * P;
+          for (int idx = threadIdx.x; idx < P; idx += blockDim.x) G[(idx / n) * LS + idx % n] = src[idx];
+          __syncthreads();
+          fft_lines<n, -1>(G, n, LS, 1, tw);    // rows
+          fft_lines<n, -1>(G, n, 1, LS, tw);    // columns
+          for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+            const int ix = idx / n, iy = idx % n;
+            const C2 z = cmulc(G[ix * LS + iy], cmul(px[ix], py[iy]));
+            C2 d = dst[idx];
+            d.x += z.x;
+            d.y += z.y;
+            dst[idx] = d;
+          }
+          __syncthreads();
         }
-        __syncthreads();
       }
     }
   }
@@ -709,10 +733,12 @@ void set_vjp_smem_attributes() {
     cudaFuncSetAttribute(k_i3_vjp_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
 }
 
-// Forward prep/I1/I2+I4 (the VJP needs wfine, D^, K2, K4^) then the transpose kernels.
+// Forward prep/I1/I2+I4 once (the VJP needs wfine, D^, K2, K4^), then per cotangent the seed and the
+// I1 and I2/I4 transposes, one I3 transpose launch for all K cotangents, and per cotangent the final
+// assembly.  Cotangent k uses copy k of every cotangent buffer of vw.
 template <int n, class T>
-cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
-                          double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,
+cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* const* lam,
+                          double* const* grad, int K, int ncells, int accumulate, cudaStream_t s, long long& launches,
                           KernelTimer* tm) {
   using C2 = typename Vec2Of<T>::type;
   set_smem_attributes<n, T>();
@@ -725,39 +751,53 @@ cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const
   C2* K4acc = (C2*)cw.K4acc;
   C2* ws = (C2*)vw.ws;
   const size_t sm = smem_bytes<n, T>();
+  constexpr size_t P = (size_t)n * n;
+  const size_t c_stride = (size_t)vw.nb * 2 * P;           // complex cotangent buffers, per cotangent
+  const size_t r_stride = (size_t)vw.nb * P;               // real cotangent buffers, per cotangent
+  const size_t nparts = (size_t)vw.nb * t.J * vw.nmc;
+  const size_t part_stride = nparts * 2 * P;
   auto begin = [&](int g) { if (tm) tm->begin(g, s); };
   auto end = [&]() { if (tm) tm->end(s); };
   begin(KG_VJP);
   k_prep<n, T><<<ncells, kThreads, sm, s>>>(w, what, wfine, ws, tb.tw);
   k_i1<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, Dacc, ws, tb.tw, tb.phip, tb.Ktab, t.J);
   k_i24<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, K2acc, K4acc, ws, tb.tw, tb.psi, t.J);
-  C2* nu = (C2*)vw.nu;
-  T* nuf = (T*)vw.nuf;
-  C2* muD = (C2*)vw.muD;
-  T* muK2 = (T*)vw.muK2;
-  C2* mu4 = (C2*)vw.mu4;
-  C2* mu3 = (C2*)vw.mu3;
-  k_vjp_seed<n, T><<<ncells, kThreads, sm, s>>>(lam, wfine, Dacc, K2acc, K4acc, nu, nuf, muD, muK2, mu4, mu3, ws,
-                                                tb.tw);
-  k_i1_vjp<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, muD, nu, nuf, ws, tb.tw, tb.phip, tb.Ktab, t.J);
-  k_i24_vjp<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, muK2, mu4, nu, nuf, ws, tb.tw, tb.psi, t.J);
+  launches += 3;
+  for (int k = 0; k < K; ++k) {
+    C2* nu = (C2*)vw.nu + k * c_stride;
+    T* nuf = (T*)vw.nuf + k * r_stride;
+    C2* muD = (C2*)vw.muD + k * c_stride;
+    T* muK2 = (T*)vw.muK2 + k * r_stride;
+    C2* mu4 = (C2*)vw.mu4 + k * c_stride;
+    C2* mu3 = (C2*)vw.mu3 + k * c_stride;
+    k_vjp_seed<n, T><<<ncells, kThreads, sm, s>>>(lam[k], wfine, Dacc, K2acc, K4acc, nu, nuf, muD, muK2, mu4, mu3,
+                                                  ws, tb.tw);
+    k_i1_vjp<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, muD, nu, nuf, ws, tb.tw, tb.phip, tb.Ktab, t.J);
+    k_i24_vjp<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, muK2, mu4, nu, nuf, ws, tb.tw, tb.psi, t.J);
+    launches += 3;
+  }
   end();
   const int nunits = ncells * t.J * vw.nmc;
   const int grid = nunits < vw.grid ? nunits : vw.grid;
   begin(KG_VJP_I3);
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
-    k_i3_vjp_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(what, wfine, mu3, (C2*)vw.part_r,
-                                                                      (C2*)vw.part_s, ws, tb.tw, tb.psip_s, tb.phase,
-                                                                      t.J, t.M, vw.nmc, vw.mch, nunits);
+    k_i3_vjp_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(
+        what, wfine, (C2*)vw.mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M, vw.nmc,
+        vw.mch, nunits, K, c_stride, part_stride);
   else
-    k_i3_vjp<n, T><<<grid, kThreads, sm, s>>>(what, wfine, mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw,
-                                              tb.psip_s, tb.phase, t.J, t.M, vw.nmc, vw.mch, nunits);
+    k_i3_vjp<n, T><<<grid, kThreads, sm, s>>>(what, wfine, (C2*)vw.mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw,
+                                              tb.psip_s, tb.phase, t.J, t.M, vw.nmc, vw.mch, nunits, K, c_stride,
+                                              part_stride);
   end();
+  ++launches;
   begin(KG_VJP);
-  k_vjp_final<n, T><<<ncells, kThreads, sm, s>>>(nu, nuf, (C2*)vw.part_r, (C2*)vw.part_s, t.J * vw.nmc, ws, tb.tw,
-                                                 grad, accumulate);
+  for (int k = 0; k < K; ++k) {
+    k_vjp_final<n, T><<<ncells, kThreads, sm, s>>>((C2*)vw.nu + k * c_stride, (T*)vw.nuf + k * r_stride,
+                                                   (C2*)vw.part_r + k * part_stride, (C2*)vw.part_s + k * part_stride,
+                                                   t.J * vw.nmc, ws, tb.tw, grad[k], accumulate);
+    ++launches;
+  }
   end();
-  launches += 8;
   return cudaGetLastError();
 }
 

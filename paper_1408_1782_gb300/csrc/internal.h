@@ -94,11 +94,15 @@ struct CollisionWork {
 };
 
 // Extra buffers of the collision operator's vector-Jacobian product
-// (collision_vjp.cuh) for a batch of nb cells; the forward intermediates
-// (what, wfine, D, K2, K4) are recomputed into the CollisionWork of the same batch.
+// (collision_vjp.cuh) for a batch of nb cells and up to kcap cotangents at once;
+// the forward intermediates (what, wfine, D, K2, K4) are recomputed into the
+// CollisionWork of the same batch.  Every cotangent buffer below holds kcap
+// copies of the shape given, one per cotangent.
+constexpr int kMaxCotangents = 4;
 struct VjpWork {
   int prec = 0;
   int nb = 0;
+  int kcap = 1;          // cotangents one product can carry
   int nmc = 1;           // m-chunks per (cell, j) unit of the I3 transpose kernel
   int mch = 1;
   int grid = 0;          // persistent grid of the I3 transpose kernel
@@ -213,17 +217,21 @@ cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cw
                        void* ws, int grid, cudaStream_t s, long long& launches);
 void free_collision_work(CollisionWork& cw);
 
-// Vector-Jacobian product of the collision operator (collision_vjp.cuh):
-// grad (+)= (dC/dW)^T lam for w, lam, grad device [nb][4][N][N]; accumulate
-// selects grad += instead of grad =.  Uses cw's forward buffers as scratch.
-cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
-                        double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,
+// Vector-Jacobian products of the collision operator (collision_vjp.cuh) at
+// one state for K <= vw.kcap cotangents: grad[k] (+)= (dC/dW)^T lam[k] for w,
+// lam[k], grad[k] device [ncells][4][N][N]; accumulate selects += instead of =.
+// The state's forward transforms are shared by the K products.  Uses cw's
+// forward buffers as scratch.
+cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* const* lam,
+                        double* const* grad, int K, int ncells, int accumulate, cudaStream_t s, long long& launches,
                         KernelTimer* tm);
-cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec = 0);
+cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec = 0, int kcap = 1);
+// How many cotangents one product should carry for this grid and precision form (1 .. kMaxCotangents).
+int vjp_cotangent_group(const Tables& t, int prec);
 void free_vjp_work(VjpWork& vw);
 template <int n, class T>
-cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* lam,
-                          double* grad, int ncells, int accumulate, cudaStream_t s, long long& launches,
+cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* const* lam,
+                          double* const* grad, int K, int ncells, int accumulate, cudaStream_t s, long long& launches,
                           KernelTimer* tm);
 template <int n, class T>
 int i3_vjp_blocks_per_sm();

@@ -165,9 +165,18 @@ int do_step(qbe_handle* h, double dt, double* snaps = nullptr) {
   return r;
 }
 
-int ensure_vjp(qbe_handle* h) {
-  if (h->vw_ready) return QBE_OK;
-  cudaError_t e = alloc_vjp_work(h->tab, h->cw.nb, h->vw, h->g.precision);
+// Adjoint workspace for products carrying up to kneed cotangents at once (grown on demand).
+int ensure_vjp(qbe_handle* h, int kneed = 1) {
+  if (h->vw_ready && h->vw.kcap >= kneed) return QBE_OK;
+  if (h->vw_ready) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint workspace resize");
+    free_vjp_work(h->vw);
+    cudaFree(h->lbuf);
+    h->lbuf = nullptr;
+    h->vw_ready = false;
+  }
+  cudaError_t e = alloc_vjp_work(h->tab, h->cw.nb, h->vw, h->g.precision, kneed);
   if (e == cudaSuccess)
     e = cudaMalloc((void**)&h->lbuf, (size_t)h->cw.nb * 4 * h->g.N * h->g.N * sizeof(double));
   if (e != cudaSuccess) {
@@ -180,49 +189,68 @@ int ensure_vjp(qbe_handle* h) {
   return QBE_OK;
 }
 
-int do_collide_vjp_dev(qbe_handle* h, const double* w, const double* lam, double* grad, int ncells, int accumulate) {
-  int r = ensure_vjp(h);
+// grad[k] (+)= (dC/dW)^T lam[k] at the state w for K <= kMaxCotangents cotangents (device
+// [ncells][4][N][N] each), in batches of cw.nb cells; the K products share the state's transforms.
+int do_collide_vjp_dev(qbe_handle* h, const double* w, const double* const* lam, double* const* grad, int K,
+                       int ncells, int accumulate) {
+  int r = ensure_vjp(h, K);
   if (r) return r;
   const size_t per = (size_t)4 * h->g.N * h->g.N;
+  const double* lk[kMaxCotangents];
+  double* gk[kMaxCotangents];
   for (int c0 = 0; c0 < ncells; c0 += h->cw.nb) {
     const int nc = (ncells - c0) < h->cw.nb ? (ncells - c0) : h->cw.nb;
-    cudaError_t e = collide_vjp(h->tab, h->cw, h->vw, w + (size_t)c0 * per, lam + (size_t)c0 * per,
-                                grad + (size_t)c0 * per, nc, accumulate, h->stream, h->launches, &h->timer);
+    for (int k = 0; k < K; ++k) {
+      lk[k] = lam[k] + (size_t)c0 * per;
+      gk[k] = grad[k] + (size_t)c0 * per;
+    }
+    cudaError_t e = collide_vjp(h->tab, h->cw, h->vw, w + (size_t)c0 * per, lk, gk, K, nc, accumulate, h->stream,
+                                h->launches, &h->timer);
     if (e != cudaSuccess) return cuda_fail(h, e, "collide vjp");
   }
   return QBE_OK;
 }
 
-// Reverse of one recorded step: *lam (cotangent of the step's output) becomes
-// the cotangent of its input; gB accumulates the field gradient.  *lam and
-// *tmp are swapped as the sweep ping-pongs between them.
-int step_vjp_one(qbe_handle* h, double dt, const double* snaps, double** lam, double** tmp, double* G1, double* lF0,
-                 double* gB, double* gsum) {
+int do_collide_vjp_dev(qbe_handle* h, const double* w, const double* lam, double* grad, int ncells, int accumulate) {
+  return do_collide_vjp_dev(h, w, &lam, &grad, 1, ncells, accumulate);
+}
+
+// Reverse of one recorded step for K <= kMaxCotangents cotangents at once: *lam[k] (cotangent of
+// the step's output) becomes the cotangent of its input; gB[k] accumulates the field gradient.
+// *lam[k] and *tmp[k] are swapped as the sweep ping-pongs between them; G1[k], lF0[k] are scratch.
+// The two collision products of the step (at W1 and at U) each serve all K cotangents.
+int step_vjp_group(qbe_handle* h, double dt, const double* snaps, double** lam, double** tmp, double* const* G1,
+                   double* const* lF0, double* const* gB, int K, double* gsum) {
   const int Nx = h->g.Nx, N = h->g.N;
   const int sA = half_substeps(h, dt);
   const double tau = 0.5 * dt / sA;
   const size_t S = state_elems(h);
-  for (int k = sA - 1; k >= 0; --k) {
-    cudaError_t e = advect_substep_vjp(snaps + (size_t)(sA + 2 + k) * S, *lam, *tmp, Nx, N, h->g.L, tau, h->bc,
-                                       gsum, h->stream, h->launches, &h->timer);
-    if (e != cudaSuccess) return cuda_fail(h, e, "advect vjp");
-    std::swap(*lam, *tmp);
-  }
+  for (int q = 0; q < K; ++q)
+    for (int k = sA - 1; k >= 0; --k) {
+      cudaError_t e = advect_substep_vjp(snaps + (size_t)(sA + 2 + k) * S, lam[q], tmp[q], Nx, N, h->g.L, tau,
+                                         h->bc, gsum, h->stream, h->launches, &h->timer);
+      if (e != cudaSuccess) return cuda_fail(h, e, "advect vjp");
+      std::swap(lam[q], tmp[q]);
+    }
   const double* U = snaps + (size_t)sA * S;
   const double* W1 = snaps + (size_t)(sA + 1) * S;
-  int r = do_collide_vjp_dev(h, W1, *lam, G1, Nx, 0);
+  int r = do_collide_vjp_dev(h, W1, lam, G1, K, Nx, 0);
   if (r) return r;
-  cudaError_t e = rk_vjp_launch(U, W1, *lam, G1, h->B, dt, lF0, *tmp, gB, Nx, N, h->stream, h->launches,
-                                &h->timer);
-  if (e != cudaSuccess) return cuda_fail(h, e, "rk vjp");
-  r = do_collide_vjp_dev(h, U, lF0, *tmp, Nx, 1);
+  for (int q = 0; q < K; ++q) {
+    cudaError_t e = rk_vjp_launch(U, W1, lam[q], G1[q], h->B, dt, lF0[q], tmp[q], gB[q], Nx, N, h->stream,
+                                  h->launches, &h->timer);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rk vjp");
+  }
+  r = do_collide_vjp_dev(h, U, lF0, tmp, K, Nx, 1);
   if (r) return r;
-  std::swap(*lam, *tmp);
-  for (int k = sA - 1; k >= 0; --k) {
-    e = advect_substep_vjp(snaps + (size_t)k * S, *lam, *tmp, Nx, N, h->g.L, tau, h->bc, gsum, h->stream,
-                           h->launches, &h->timer);
-    if (e != cudaSuccess) return cuda_fail(h, e, "advect vjp");
-    std::swap(*lam, *tmp);
+  for (int q = 0; q < K; ++q) {
+    std::swap(lam[q], tmp[q]);
+    for (int k = sA - 1; k >= 0; --k) {
+      cudaError_t e = advect_substep_vjp(snaps + (size_t)k * S, lam[q], tmp[q], Nx, N, h->g.L, tau, h->bc, gsum,
+                                         h->stream, h->launches, &h->timer);
+      if (e != cudaSuccess) return cuda_fail(h, e, "advect vjp");
+      std::swap(lam[q], tmp[q]);
+    }
   }
   return QBE_OK;
 }
@@ -504,6 +532,29 @@ int qbe_collide_vjp(qbe_handle* h, const double* w, const double* lam, double* g
   return QBE_OK;
 }
 
+int qbe_collide_vjp_n(qbe_handle* h, int ncot, const double* w, const double* lam, double* grad, int ncells,
+                      int on_device) {
+  if (!h) return QBE_ERR_ARG;
+  if (!w || !lam || !grad || ncells < 1 || ncot < 1)
+    return fail(h, QBE_ERR_ARG, "collide_vjp_n: null pointer, ncells < 1 or ncot < 1");
+  if (on_device != 1) return fail(h, QBE_ERR_ARG, "collide_vjp_n: device memory only");
+  DeviceGuard dg(h->g.device);
+  const size_t per = (size_t)ncells * 4 * h->g.N * h->g.N;
+  const double* lk[kMaxCotangents];
+  double* gk[kMaxCotangents];
+  const int kg = vjp_cotangent_group(h->tab, h->g.precision);
+  for (int k0 = 0; k0 < ncot; k0 += kg) {
+    const int K = (ncot - k0) < kg ? (ncot - k0) : kg;
+    for (int k = 0; k < K; ++k) {
+      lk[k] = lam + (size_t)(k0 + k) * per;
+      gk[k] = grad + (size_t)(k0 + k) * per;
+    }
+    const int r = do_collide_vjp_dev(h, w, lk, gk, K, ncells, 0);
+    if (r) return r;
+  }
+  return QBE_OK;
+}
+
 int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_every) {
   if (!h) return QBE_ERR_ARG;
   if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
@@ -545,21 +596,30 @@ int qbe_step_vjp_n(qbe_handle* h, int ncot, const double* lam_final, double* lam
   const size_t nb3 = (size_t)Nx * 3;
   const int sA = half_substeps(h, dt);
   const size_t per_step = (size_t)(2 * sA + 2) * S;
-  int r = ensure_vjp(h);
+  // cotangents travel through the sweep in groups (vjp_cotangent_group: up to four, or one for the
+  // FP32 shared-memory transpose)
+  const int kmax = vjp_cotangent_group(h->tab, h->g.precision);
+  const int kg = ncot < kmax ? ncot : kmax;
+  int r = ensure_vjp(h, kg);
   if (r) return r;
   if (h->snaps.ensure((size_t)every * per_step) != cudaSuccess ||
-      h->adj.ensure((2 * (size_t)ncot + 3) * S) != cudaSuccess || h->small.ensure(small_elems(h)) != cudaSuccess ||
-      h->gradb.ensure((size_t)ncot * nb3) != cudaSuccess)
+      h->adj.ensure((2 * (size_t)ncot + 2 * (size_t)kg + 1) * S) != cudaSuccess ||
+      h->small.ensure(small_elems(h)) != cudaSuccess || h->gradb.ensure((size_t)ncot * nb3) != cudaSuccess)
     return fail(h, QBE_ERR_ALLOC, "adjoint sweep storage");
-  // per cotangent k: lam[k], tmp[k] (ping-pong); shared: G1, lF0, the final state
-  std::vector<double*> lam(ncot), tmp(ncot);
+  // per cotangent k: lam[k], tmp[k] (ping-pong); per group slot q: G1[q], lF0[q]; the final state
+  std::vector<double*> lam(ncot), tmp(ncot), gBk(ncot);
   for (int k = 0; k < ncot; ++k) {
     lam[k] = h->adj.p + (size_t)(2 * k) * S;
     tmp[k] = h->adj.p + (size_t)(2 * k + 1) * S;
+    gBk[k] = h->gradb.p + (size_t)k * nb3;
   }
-  double* G1 = h->adj.p + (size_t)(2 * ncot) * S;
-  double* lF0 = G1 + S;
-  double* Wfin = lF0 + S;
+  double* G1[kMaxCotangents];
+  double* lF0[kMaxCotangents];
+  for (int q = 0; q < kg; ++q) {
+    G1[q] = h->adj.p + (size_t)(2 * ncot + 2 * q) * S;
+    lF0[q] = G1[q] + S;
+  }
+  double* Wfin = h->adj.p + (size_t)(2 * ncot + 2 * kg) * S;
   double* gsum = h->small.p;
   const size_t sb = S * sizeof(double);
   const cudaMemcpyKind in_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -581,9 +641,10 @@ int qbe_step_vjp_n(qbe_handle* h, int ncot, const double* lam_final, double* lam
       if (r) return r;
     }
     for (int i = len - 1; i >= 0; --i)
-      for (int k = 0; k < ncot; ++k) {
-        r = step_vjp_one(h, dt, h->snaps.p + (size_t)i * per_step, &lam[k], &tmp[k], G1, lF0,
-                         h->gradb.p + (size_t)k * nb3, gsum);
+      for (int k0 = 0; k0 < ncot; k0 += kg) {
+        const int K = (ncot - k0) < kg ? (ncot - k0) : kg;
+        r = step_vjp_group(h, dt, h->snaps.p + (size_t)i * per_step, &lam[k0], &tmp[k0], G1, lF0, &gBk[k0], K,
+                           gsum);
         if (r) return r;
       }
   }

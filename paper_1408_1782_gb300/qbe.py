@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libqbe.so")
 
 QBE_PERIODIC, QBE_DIRICHLET, QBE_MAXWELL = 0, 1, 2
+QBE_OK, QBE_ERR_ARG = 0, -1
 _BC = {"periodic": QBE_PERIODIC, "dirichlet": QBE_DIRICHLET, "maxwell": QBE_MAXWELL}
 
 # Every entry point declared in include/qbe.h, with its ctypes signature.
@@ -61,6 +62,7 @@ SIGNATURES = {
     "qbe_enable_timing": (_c_int, [_c_void_p, _c_int]),
     "qbe_kernel_time": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "qbe_collide_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int, _c_int]),
+    "qbe_collide_vjp_n": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_int, _c_int]),
     "qbe_step_checkpointed": (_c_int, [_c_void_p, _c_double, _c_int, _c_int]),
     "qbe_step_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_step_vjp_n": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_int]),
@@ -321,6 +323,21 @@ class Solver:
             raise ValueError("w, lam and out must all be host or all be device memory")
         self._check(lib().qbe_collide_vjp(self._h, _c_void_p(pw), _c_void_p(pl), _c_void_p(po), ncells, dev),
                     "qbe_collide_vjp")
+        return out
+
+    def collide_vjp_many(self, w, lams, out=None):
+        """(dC/dW at w)^T lams[k] for a stack of cotangents lams[ncot][ncells][4][N][N] (CUDA tensors;
+        the products share the state's transforms in groups of up to four)."""
+        ncells, ncot = w.shape[0], lams.shape[0]
+        shape = (ncells, 4, self.N, self.N)
+        pw, dev, k1 = _arg(w, shape)
+        pl, dev2, k2 = _arg(lams, (ncot,) + shape)
+        out = self._like(lams, (ncot,) + shape, out)
+        po, dev3, k3 = _arg(out, (ncot,) + shape)
+        if not (dev and dev2 and dev3):
+            raise ValueError("qbe_collide_vjp_n takes device memory")
+        self._check(lib().qbe_collide_vjp_n(self._h, ncot, _c_void_p(pw), _c_void_p(pl), _c_void_p(po), ncells, 1),
+                    "qbe_collide_vjp_n")
         return out
 
     def step_checkpointed(self, dt, nsteps, checkpoint_every=20):

@@ -126,6 +126,29 @@ def test_collide_vjp_fp32_split_matches_fp64_n64(qbe):
     assert err < 5e-6, err
 
 
+@pytest.mark.parametrize("precision,N", [(0, 8), (1, 16), (1, 48), (1, 96)])
+def test_collide_vjp_many_equals_single_products(qbe, precision, N):
+    """qbe_collide_vjp_n: five cotangents at one state give exactly the single products.  The staged
+    transpose kernels (FP64 at N = 8, FP32 at N = 96) carry them as a group of four sharing the state's
+    transforms and a group of one; the FP32 shared-memory kernel (N = 16, 48) one at a time."""
+    import torch
+
+    J, M, ncells, ncot = 4, 3, 3, 5
+    w = inputs.synthetic_w(N, ncells, seed=71, perturb=0.05)
+    lams = np.stack([inputs.random_field(w.shape, seed=72 + k) for k in range(ncot)])
+    s = qbe.Solver(N, ncells, J=J, M=M, precision=precision)
+    wd = torch.from_numpy(w).cuda()
+    got = s.collide_vjp_many(wd, torch.from_numpy(lams).cuda()).cpu().numpy()
+    for k in range(ncot):
+        one = s.collide_vjp(w, lams[k])
+        assert np.array_equal(got[k], one), k
+    # argument errors: null pointers, host memory
+    assert qbe.lib().qbe_collide_vjp_n(s._h, 2, None, None, None, ncells, 1) == qbe.QBE_ERR_ARG
+    assert qbe.lib().qbe_collide_vjp_n(s._h, 1, w.ctypes.data, lams.ctypes.data, lams.ctypes.data, ncells,
+                                       0) == qbe.QBE_ERR_ARG
+    s.close()
+
+
 def test_collide_vjp_batches_and_device_memory(qbe):
     """More cells than one batch of the handle, device pointers, grad aliasing lam."""
     import torch
@@ -327,20 +350,26 @@ def test_autograd_functions(qbe):
     s.close()
 
 
-def test_step_vjp_for_several_cotangents_in_one_sweep(qbe):
-    """One reverse sweep for both observables equals two single sweeps, bitwise."""
-    N, Nx, J, M = 8, 4, 4, 2
+@pytest.mark.parametrize("precision,N,ncot", [(0, 8, 2), (1, 16, 5)])
+def test_step_vjp_for_several_cotangents_in_one_sweep(qbe, precision, N, ncot):
+    """One reverse sweep for several cotangents equals one sweep per cotangent, bitwise: the
+    cotangents of a group share the state's transforms of each collision product but none of their
+    own arithmetic.  Precision 0 (staged FP64 transpose) carries the two cotangents as one group;
+    precision 1 at N = 16 (shared-memory FP32 transpose) sweeps five cotangents one at a time."""
+    Nx, J, M = 4, 4, 2
     W = inputs.synthetic_w(N, Nx, seed=97, perturb=0.05)
     B = inputs.uniform_b(Nx, (0.1, -0.3, 0.2))
-    s = gpu_solver(qbe, N, Nx, J, M, "maxwell", R=2.0)
+    s = gpu_solver(qbe, N, Nx, J, M, "maxwell", precision=precision, R=2.0)
     s.set_state(W)
     s.set_bfield(B)
     s.step_checkpointed(0.01, 5, 2)
-    lams = np.stack([s.observables_vjp(np.array([1.0, 0.0])), s.observables_vjp(np.array([0.0, 1.0]))])
+    lams = [s.observables_vjp(np.array([1.0, 0.0])), s.observables_vjp(np.array([0.0, 1.0]))]
+    lams += [inputs.random_field(W.shape, seed=98 + k) for k in range(ncot - 2)]
+    lams = np.stack(lams)
     l0, gb = s.step_vjp_many(lams)
-    for k in range(2):
+    for k in range(ncot):
         a, b = s.step_vjp(lams[k].copy())
-        assert np.array_equal(a, l0[k]) and np.array_equal(b, gb[k])
+        assert np.array_equal(a, l0[k]) and np.array_equal(b, gb[k]), k
     s.close()
 
 
