@@ -248,24 +248,19 @@ __global__ void __launch_bounds__(kThreads) k_i24(const typename Vec2Of<T>::type
 // The unit's partial sum acc[2][n*n] (pairs (0,1), (2,3), real space) is
 // written to its own slot of K3part and reduced in fixed order later.
 // --------------------------------------------------------------------------
-// Launch shape of the staged I3 kernel: three 256-thread blocks per SM with 64 KB chunks, except
-// FP32 on padded grids above 128 points (where the field does not fit one block's shared memory):
-// one 1024-thread block per SM with 128 KB chunks, more warps to hide the scratch round trips.
-template <int n, class T>
-__host__ __device__ constexpr bool i3_wide() {
-  return std::is_same<T, float>::value && n > 128;
-}
+// Launch shape of the staged I3 kernel (FP64 on every grid; the FP32-split form uses k_i3_smem up
+// to 128 points and k_i3_cluster above): three 256-thread blocks per SM with 64 KB chunks.
 template <int n, class T>
 __host__ __device__ constexpr int i3_threads() {
-  return i3_wide<n, T>() ? 1024 : kThreads;
+  return kThreads;
 }
 template <int n, class T>
 __host__ __device__ constexpr int i3_min_blocks() {
-  return i3_wide<n, T>() ? 1 : 3;
+  return 3;
 }
 template <int n, class T>
 __host__ __device__ constexpr int i3_chunk_bytes() {
-  return i3_wide<n, T>() ? 131072 : 65536;
+  return 65536;
 }
 
 template <int n, class T>
@@ -470,6 +465,191 @@ constexpr size_t i3_smem_bytes() {   // twiddles, the field (padded rows), psi'_
 }
 
 // --------------------------------------------------------------------------
+// I3 on padded grids above 128 points in FP32 (n = 192, 256: one field is 288 or 512 KB, more
+// than one block's shared memory).  A cluster of kI3Cluster CTAs works on one unit at a time:
+// CTA r holds rows [r R, r R + R) of the transform field (R = n / kI3Cluster) for the row
+// transforms and columns [r R, r R + R) for the column psi' convolution, with the angle's psi'
+// columns in shared memory.  The transposes between the two go through the cluster's field in
+// global memory, ordered by cluster barriers; per cluster that field and the two shifted fields
+// (3 n^2 complex values) stay L2-resident, where 152 independent units of the staged kernel
+// (about 2.5 MB each) would not.  Same units, line transforms and accumulation order as k_i3,
+// so the results are bitwise identical.  Every CTA of a cluster runs the same loop trip counts,
+// so every barrier is reached by all of them (hardware barriers, no spin waits).
+// --------------------------------------------------------------------------
+// Measured at N = 128 (32 cells, C[W] I3 launch): 4 CTAs x 1024 threads 239.9 ms; 8 CTAs x 512
+// threads (two CTAs of different clusters per SM) 255.4 ms; the staged k_i3 294.5 ms.
+constexpr int kI3Cluster = 4;             // CTAs per cluster
+constexpr int kThreadsI3Cluster = 1024;   // threads per CTA
+
+template <int n>
+__host__ __device__ constexpr bool use_i3_cluster() {
+  return n > 128;
+}
+
+template <int n>
+__host__ __device__ constexpr int i3_cluster_slab() {   // complex elements of the row / column slab
+  constexpr int R = n / kI3Cluster;
+  return R * (n + 1) > n * R ? R * (n + 1) : n * R;
+}
+
+template <int n>
+constexpr size_t i3_cluster_smem_bytes() {   // twiddles, the slab, psi' columns
+  return (size_t)(n + i3_cluster_slab<n>()) * sizeof(float2) + (size_t)n * (n / kI3Cluster) * sizeof(float);
+}
+
+__device__ __forceinline__ int cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+__device__ __forceinline__ int cluster_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return (int)r;
+}
+__device__ __forceinline__ int cluster_count() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return (int)r;
+}
+// All threads of all CTAs of the cluster.  The arrive has release and the wait acquire semantics at
+// cluster scope, so global writes made before it by any thread of the cluster are visible after it
+// to every thread of the cluster; reads of another CTA's writes use ld.global.cg (L2, the point of
+// coherence) so that no stale L1 line can serve them.
+__device__ __forceinline__ void cluster_sync_global() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int n>
+__global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3Cluster, 1024 / kThreadsI3Cluster)
+    k_i3_cluster(const I3Jobs<float> jobs, float2* ws, const float2* __restrict__ gtw) {
+  static_assert(n / kI3Cluster * n >= kThreadsI3Cluster, "at least one element per thread in every phase");
+  using C2 = float2;
+  constexpr int R = n / kI3Cluster, LS = n + 1, P = n * n;
+  constexpr int XC = (n / 2) / kI3Cluster;           // Xi columns per CTA in the shift transforms
+  static_assert(n % kI3Cluster == 0 && (n / 2) % kI3Cluster == 0, "cluster split");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);
+  C2* F = tw + n;                                    // [R][LS] row slab, [n][R] or [n][XC] column slab
+  float* psl = reinterpret_cast<float*>(F + i3_cluster_slab<n>());   // psi'_j of this CTA's columns, [n][R]
+  __shared__ int xcols[n];
+  __shared__ unsigned char xmask[n];
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int pos = 0; pos < n; ++pos) {
+      const int k = freq_of_pos<n>(pos);
+      const bool in = (k < n / 4) || (k >= n - n / 4);
+      xmask[pos] = in ? 1 : 0;
+      if (in) xcols[cnt++] = pos;
+    }
+  }
+  load_twiddles<n>(tw, gtw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int rank = cluster_rank();
+  const int r0 = rank * R;                           // this CTA's first row / column
+  C2* Gs = ws + (size_t)cluster_index() * 3 * P;     // the cluster's transform field
+  C2* Sig = Gs + P;                                  // the two shifted pairs
+  for (int gunit = cluster_index(); gunit < jobs.total; gunit += cluster_count()) {
+    const I3Job<float>& jb = jobs.job[i3_job_of(jobs, gunit)];
+    const int unit = gunit - jb.unit_begin;
+    const int J = jb.J, M = jb.M, nmc = jb.nmc, mch = jb.mch;
+    const C2* what = jb.what;
+    const C2* __restrict__ phase = jb.phase;
+    const int c = unit / (J * nmc);
+    const int j = (unit / nmc) % J;
+    const int mc = unit % nmc;
+    C2* acc = jb.K3part + (size_t)unit * 2 * P;
+    for (int idx = tid; idx < R * n; idx += nt) {
+      acc[(size_t)r0 * n + idx] = zero2<float>();
+      acc[P + (size_t)r0 * n + idx] = zero2<float>();
+    }
+    const float* __restrict__ psp = jb.psip_s + (size_t)j * P;
+    for (int idx = tid; idx < n * R; idx += nt) psl[idx] = psp[(idx / R) * n + r0 + idx % R];
+    __syncthreads();
+    const C2* wf = jb.wfine + (size_t)c * 2 * P;
+    const int m0 = mc * mch, m1 = min(M, m0 + mch);
+    for (int m = m0; m < m1; ++m) {
+      const C2* px = phase + ((size_t)j * M + m) * 2 * n;
+      const C2* py = px + n;
+      cluster_sync_global();                         // the previous m's (or unit's) Sig and Gs are read
+      // shifted fields, column transforms over this CTA's share of the Xi columns
+      for (int p = 0; p < 2; ++p) {
+        const C2* in = what + ((size_t)c * 4 + p) * P;
+        C2* S = Sig + (size_t)p * P;
+        for (int idx = tid; idx < n * XC; idx += nt) {
+          const int ix = idx / XC, cc = idx % XC, iy = xcols[rank * XC + cc];
+          F[idx] = xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<float>();
+        }
+        __syncthreads();
+        fft_lines<n, 1>(F, XC, 1, XC, tw);
+        for (int idx = tid; idx < n * XC; idx += nt) {
+          const int ix = idx / XC, cc = idx % XC;
+          S[ix * n + xcols[rank * XC + cc]] = F[idx];
+        }
+        __syncthreads();
+      }
+      cluster_sync_global();                         // the Xi columns of both shifted fields are complete
+      // row transforms over this CTA's rows (columns outside Xi are zero)
+      for (int p = 0; p < 2; ++p) {
+        C2* S = Sig + (size_t)p * P + (size_t)r0 * n;
+        for (int idx = tid; idx < R * n; idx += nt) {
+          const int r = idx / n, iy = idx % n;
+          F[r * LS + iy] = xmask[iy] ? __ldcg(&S[idx]) : zero2<float>();
+        }
+        __syncthreads();
+        fft_lines<n, 1>(F, R, LS, 1, tw);
+        for (int idx = tid; idx < R * n; idx += nt) S[idx] = F[(idx / n) * LS + idx % n];
+        __syncthreads();
+      }
+      // from here on this CTA reads only its own rows of the shifted fields
+      for (int a = 0; a < 4; ++a) {
+        const C2* wa = wf + (size_t)(a >> 1) * P + (size_t)r0 * n;
+        const C2* Sa = Sig + (size_t)(a >> 1) * P + (size_t)r0 * n;
+        const bool im = (a & 1) != 0;
+        const float eta = (a == 0) ? 1.f : -1.f;
+        for (int p = 0; p < 2; ++p) {
+          const C2* Sp = Sig + (size_t)p * P + (size_t)r0 * n;
+          C2* accp = acc + (size_t)p * P + (size_t)r0 * n;
+          // forward row transforms of w_a S_pair on this CTA's rows
+#pragma unroll 4
+          for (int idx = tid; idx < R * n; idx += nt) {
+            const C2 z = wa[idx];
+            F[(idx / n) * LS + idx % n] = cscale(Sp[idx], im ? z.y : z.x);
+          }
+          __syncthreads();
+          fft_lines<n, -1>(F, R, LS, 1, tw);
+#pragma unroll 4
+          for (int idx = tid; idx < R * n; idx += nt) Gs[(size_t)r0 * n + idx] = F[(idx / n) * LS + idx % n];
+          cluster_sync_global();                     // all rows transformed
+          // column psi' convolution on this CTA's columns
+#pragma unroll 4
+          for (int idx = tid; idx < n * R; idx += nt) F[idx] = __ldcg(&Gs[(idx / R) * n + r0 + idx % R]);
+          __syncthreads();
+          fft_conv_lines<n>(F, R, 1, R, tw, [&](int l, int pos) { return psl[pos * R + l]; });
+#pragma unroll 4
+          for (int idx = tid; idx < n * R; idx += nt) Gs[(idx / R) * n + r0 + idx % R] = F[idx];
+          cluster_sync_global();                     // all columns convolved
+          // inverse row transforms on this CTA's rows, accumulated with eta_a S_a
+#pragma unroll 4
+          for (int idx = tid; idx < R * n; idx += nt) F[(idx / n) * LS + idx % n] = __ldcg(&Gs[(size_t)r0 * n + idx]);
+          __syncthreads();
+          fft_lines<n, 1>(F, R, LS, 1, tw);
+#pragma unroll 4
+          for (int idx = tid; idx < R * n; idx += nt) {
+            const C2 v = F[(idx / n) * LS + idx % n];
+            const C2 sv = Sa[idx];
+            const float f = eta * (im ? sv.y : sv.x);
+            const C2 d = accp[idx];
+            accp[idx] = mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y));
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
 // Assemble C on the fine grid from D, K2, K3, K4 (Pauli formulas of Sec. 3.1),
 // then FFT, cut to Xi (without the -N/2 line), inverse FFT and sample the
 // coarse nodes.  One block per cell.  The K3 partial sums are added in FP64.
@@ -577,10 +757,35 @@ void set_smem_attributes() {
   cudaFuncSetAttribute(k_prep<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i1<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i24<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_i3<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_staged_smem_bytes<n, T>());
   cudaFuncSetAttribute(k_assemble<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     cudaFuncSetAttribute(k_i3_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
+  else if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>())
+    cudaFuncSetAttribute(k_i3_cluster<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)i3_cluster_smem_bytes<n>());
+  else
+    cudaFuncSetAttribute(k_i3<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_staged_smem_bytes<n, T>());
+}
+
+// Clusters of k_i3_cluster<n> that can be resident at once on the current device (cached per device).
+template <int n>
+int i3_max_clusters() {
+  static int cached[64] = {};
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  if (cached[dev & 63] > 0) return cached[dev & 63];
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kI3Cluster * (nsm > 0 ? nsm : 1));
+  cfg.blockDim = dim3(kThreadsI3Cluster);
+  cfg.dynamicSmemBytes = i3_cluster_smem_bytes<n>();
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_i3_cluster<n>, &cfg) != cudaSuccess || ncl < 1) {
+    cudaGetLastError();
+    ncl = (nsm > 0 ? nsm : 1) / kI3Cluster;
+  }
+  cached[dev & 63] = ncl < 1 ? 1 : ncl;
+  return cached[dev & 63];
 }
 
 template <int n, class T>
@@ -589,6 +794,9 @@ int i3_blocks_per_sm() {
   int b = 0;
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>());
+  else if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>())
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_cluster<n>, kThreadsI3Cluster,
+                                                  i3_cluster_smem_bytes<n>());
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n, T>, i3_threads<n, T>(), i3_staged_smem_bytes<n, T>());
   return b < 1 ? 1 : b;
@@ -642,7 +850,8 @@ I3Job<T> i3_job(const Tables& t, const CollisionWork& cw, int ncells, int unit_b
 }
 
 // I3 over the units of njobs simulations (same n and precision, njobs <= kMaxI3Jobs); ws must hold
-// 3 (2N)^2 complex values for each of `grid` blocks.
+// 3 (2N)^2 complex values for each of `grid` blocks (the cluster form uses one such slot per cluster
+// of kI3Cluster blocks).
 template <int n, class T>
 cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
                        void* ws, int grid, cudaStream_t s, long long& launches) {
@@ -660,10 +869,18 @@ cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cw
   if (total == 0) return cudaSuccess;
   const int g = total < grid ? total : grid;
   const TabPtrs<T> tb = tab_ptrs<T>(*tabs[0]);
-  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>()) {
     k_i3_smem<n><<<g, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(jobs, (C2*)ws, tb.tw);
-  else
+  } else if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
+    int ncl = grid / kI3Cluster;
+    const int cmax = i3_max_clusters<n>();
+    if (ncl > cmax) ncl = cmax;
+    if (ncl > total) ncl = total;
+    if (ncl < 1) ncl = 1;
+    k_i3_cluster<n><<<ncl * kI3Cluster, kThreadsI3Cluster, i3_cluster_smem_bytes<n>(), s>>>(jobs, (C2*)ws, tb.tw);
+  } else {
     k_i3<n, T><<<g, i3_threads<n, T>(), i3_staged_smem_bytes<n, T>(), s>>>(jobs, (C2*)ws, tb.tw);
+  }
   ++launches;
   return cudaGetLastError();
 }

@@ -14,6 +14,8 @@ CASES = [  # N, Nx, bc, precision
     (8, 6, "maxwell", 0),
     (16, 4, "periodic", 1),
     (48, 2, "maxwell", 0),
+    (96, 2, "maxwell", 1),
+    (128, 2, "periodic", 1),
 ]
 
 

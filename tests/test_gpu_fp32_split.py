@@ -62,6 +62,17 @@ def test_fp32_split_collision_against_oracle(qbe, N, J, M, ncells):
     assert mx < TOL_MAX and l1 < TOL_L1, (mx, l1)
 
 
+def test_fp32_split_cluster_grids(qbe):
+    """Padded grids above 128 points (N = 96, 128), where a cluster of CTAs shares each I3 unit: N = 96
+    against the oracle, N = 128 (three cells, several units per cell) against the FP64 GPU form."""
+    w = inputs.synthetic_w(96, 1, seed=21, perturb=0.05)
+    mx, l1 = errors(collide(qbe, w, 96, 4, 4, 1), O.collision(w, O.Params(N=96, J=4, M=4)))
+    assert mx < TOL_MAX and l1 < TOL_L1, (mx, l1)
+    w = inputs.synthetic_w(128, 3, seed=22, perturb=0.05)
+    mx, l1 = errors(collide(qbe, w, 128, 8, 6, 1), collide(qbe, w, 128, 8, 6, 0))
+    assert mx < TOL_MAX and l1 < TOL_L1, (mx, l1)
+
+
 @pytest.mark.parametrize("name", ["plain_fp64_n64_cells.npz", "precision_n128_cells.npz"])
 def test_fp32_split_collision_on_stored_oracle_cells(qbe, name):
     """N = 64 and N = 128 cells of the at-scale workloads (J = M = 32)."""
