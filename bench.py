@@ -358,7 +358,8 @@ def run_ours(args):
             "dtype": "f64" if prec == 0 else "f32-split",
             "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)",
             "config": config_dict(wl, world),
-            "roofline": {"kernel": "k_i3 (Hu-Ying I3 term)", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": ("k_i3" if prec == 0 else ("k_i3_smem" if N <= 64 else "k_i3_cluster"))
+                                   + " (Hu-Ying I3 term)", "bound": "alu", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": (I3_DRAM_BYTES_PER_UNIT[(N, prec)] * Nx * wl["J"] * wl["M"]
                                      if (N, prec) in I3_DRAM_BYTES_PER_UNIT else None),
