@@ -40,12 +40,12 @@ sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
-FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (profiles/fp64_fp32_issue_rates.md)
+FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (an issue-rate microbenchmark)
 FP32_FMA_PER_CLK_PER_SM = 128        # measured 116 FFMA/clk/SM
-# DRAM bytes (read + write) per (cell, j, m) unit of the I3 kernel from one ncu capture of an 8-cell
-# slice of the current kernel (profiles/k_i3_f64_n64_8cells.md, profiles/k_i3_smem_f32_n64_8cells.md),
-# scaled by units; absent for sizes with no capture of the current kernel.
-I3_DRAM_BYTES_PER_UNIT = {(64, 0): 119.85e9 / 8192, (64, 1): 5.548e9 / 8192}
+# DRAM bytes (read + write) per (cell, j, m) unit of the I3 kernel from one ncu capture of a slice of
+# the current kernel (8 cells at N = 64 in FP64 and FP32, 4 cells at N = 128 in FP32), scaled by units;
+# absent for sizes with no capture of the current kernel.
+I3_DRAM_BYTES_PER_UNIT = {(64, 0): 119.85e9 / 8192, (64, 1): 5.548e9 / 8192, (128, 1): 29.669e9 / 4096}
 
 
 def workload(name="plain_fp64_n64", precision=None):
