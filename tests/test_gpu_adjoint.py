@@ -126,6 +126,23 @@ def test_collide_vjp_fp32_split_matches_fp64_n64(qbe):
     assert err < 5e-6, err
 
 
+def test_collide_vjp_fp32_split_matches_fp64_largest_grid(qbe):
+    """N = 128 (the staged FP32 transpose on the 256-point grid), two cotangents in one product
+    against the FP64 form's single products."""
+    import torch
+
+    N, J, M, ncells = 128, 4, 4, 2
+    W = inputs.synthetic_w(N, ncells, seed=31, perturb=0.05)
+    lams = np.stack([inputs.random_field(W.shape, seed=32 + k) for k in range(2)])
+    s = qbe.Solver(N, ncells, J=J, M=M, precision=1)
+    g32 = s.collide_vjp_many(torch.from_numpy(W).cuda(), torch.from_numpy(lams).cuda()).cpu().numpy()
+    s.close()
+    for k in range(2):
+        g64 = vjp(qbe, W, lams[k], N, J, M, 0)
+        err = np.abs(g32[k] - g64).max() / np.abs(g64).max()
+        assert err < 5e-6, (k, err)
+
+
 @pytest.mark.parametrize("precision,N", [(0, 8), (1, 16), (1, 48), (1, 96)])
 def test_collide_vjp_many_equals_single_products(qbe, precision, N):
     """qbe_collide_vjp_n: five cotangents at one state give exactly the single products.  The staged
