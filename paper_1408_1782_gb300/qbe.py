@@ -6,6 +6,19 @@ CPU fallback.  If the library has not been built, importing ``lib()`` raises.
 Arrays: numpy float64 arrays are passed as host memory (the library copies
 them); CUDA torch tensors (float64, contiguous) are passed as device memory.
 State layout: ``w[cell][4][ix][iy]`` Pauli components, v = (2L/N)(ix-N/2, iy-N/2).
+
+Example (ten split steps of the N = 64, Nx = 128 workload with Dirichlet walls)::
+
+    from paper_1408_1782_gb300 import inputs, qbe
+    s = qbe.Solver(64, 128, J=32, M=32)                  # precision=1: the FP32-split form
+    wall = qbe.fd_state(1.0, 0.0, 0.0)                   # Fermi-Dirac inflow, beta = 1, mu = 0
+    s.set_boundary("dirichlet", wall, wall)
+    s.set_state(inputs.synthetic_w(64, 128, seed=0, perturb=0.05))
+    s.set_bfield(inputs.uniform_b(128, (0.0, 0.0, 0.5)))
+    s.step(0.005, 10)
+    W = s.get_state()                                    # numpy [128][4][64][64]
+    rho, momentum, energy = s.moments()
+    s.close()
 """
 from __future__ import annotations
 
