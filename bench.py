@@ -526,14 +526,22 @@ def run_collide_only(args, wl, local):
     return 0
 
 
-def i3_vjp_flops_per_unit(N):
-    """Algorithmic FLOPs of one (cell, j, m) unit of the I3 transpose kernel, same convention as
-    i3_flops_per_unit: 72 real 2-D transforms (4 for the two shifts, 64 for the 16 convolutions of
-    complex pairs, 4 for the two forward transforms of the shifted-back sums) at 2.5 P log2 P each,
-    plus 228 P pointwise flops (shift phases, 16 scalings, 16 psi' products, the three pointwise
-    sums per component, the conjugate phases and spectral accumulation)."""
+def i3_vjp_flops_per_unit(N, K=1):
+    """Algorithmic FLOPs of one (cell, j, m) unit of the I3 transpose kernel carrying K cotangents,
+    same convention as i3_flops_per_unit.  Per cotangent: 72 real 2-D transforms (4 for the two
+    shifts, 64 for the 16 convolutions of complex pairs, 4 for the two forward transforms of the
+    shifted-back sums) at 2.5 P log2 P each, plus 228 P pointwise flops (shift phases, 16 scalings,
+    16 psi' products, the three pointwise sums per component, the conjugate phases and spectral
+    accumulation).  K cotangents at one state share the shifts and the 8 convolutions of the state
+    (36 real transforms), so the launch does 36 + 36 K of them."""
     P = (2 * N) ** 2
-    return 180.0 * P * math.log2(P) + 228.0 * P
+    return 2.5 * P * math.log2(P) * (36.0 + 36.0 * K) + 228.0 * P * K
+
+
+def vjp_cotangent_group(prec, N, ncot):
+    """Cotangents one collision product carries in the library (the FP32-split form on padded grids
+    up to 128 points takes one at a time, the staged forms up to four)."""
+    return 1 if (prec == 1 and 2 * N <= 128) else min(ncot, 4)
 
 
 def run_adjoint(args, local):
@@ -608,7 +616,8 @@ def run_adjoint(args, local):
     # reverse work per observable gradient (two gradients share one sweep) over the forward sweep
     ratio = (rev / 2.0) / fwd
     avg_vi3 = vi3_ms * 1e-3 / max(vi3_n, 1)
-    flops = Nx * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N)
+    kgrp = vjp_cotangent_group(prec, N, 2)            # the sweep carries two cotangents
+    flops = Nx * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N, kgrp)
     sm_max = 2070.0
     try:
         sm_max = float(json.load(open(MEASURED_PEAKS)).get("sm_max_mhz", sm_max))
@@ -729,13 +738,14 @@ def run_vjp_only(args, wl, local):
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
     v_ms, v_n = s.kernel_time("vjp_i3")
-    # one I3 transpose launch carries all K products (up to four); work per product as for K = 1
-    flops = K * cells * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N)
+    # one I3 transpose launch carries a group of the K products; algorithmic work of such a launch
+    kgrp = vjp_cotangent_group(wl.get("precision", 0), N, K)
+    flops = cells * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N, kgrp)
     line = {"mode": "vjp", "metric": "dC/dW^T products, cell·k-pts/s",
             "value": K * args.steps * cells * N * N / (t_ms * 1e-3),
             "unit": "cell·k-pts/s", "cells": cells, "cotangents": K, "steps": args.steps, "warmup": args.warmup,
             "ms_per_product": t_ms / args.steps / K, "vjp_i3_ms_per_launch": v_ms / max(v_n, 1),
-            "vjp_i3_tflops_per_product_convention": flops / (v_ms / max(v_n, 1) * 1e-3) / 1e12,
+            "cotangents_per_launch": kgrp, "vjp_i3_tflops": flops / (v_ms / max(v_n, 1) * 1e-3) / 1e12,
             "dtype": "f64" if wl.get("precision", 0) == 0 else "f32-split", "workload": wl["name"]}
     print(json.dumps(line), flush=True)
     s.close()
