@@ -224,7 +224,8 @@ cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec, int k
   QBE_ALLOC(vw.mu4, kc * nb * 2 * P * cz);
   QBE_ALLOC(vw.mu3, kc * nb * 2 * P * cz);
   QBE_ALLOC(vw.part_r, kc * nparts * 2 * P * cz);
-  QBE_ALLOC(vw.part_s, kc * nparts * 2 * P * cz);
+  const size_t Q = (size_t)(t.n / 2 - 1) * (t.n / 2 - 1);   // kept frequencies (Fourier-space partials)
+  QBE_ALLOC(vw.part_s, kc * nparts * 2 * Q * cz);
   QBE_ALLOC(vw.ws, ws_fields * P * cz);
 #undef QBE_ALLOC
   return cudaSuccess;

@@ -321,6 +321,27 @@ __global__ void __launch_bounds__(kThreads) k_i24_vjp(
   }
 }
 
+// The Fourier-space partials of the I3 transpose are kept only on the frequencies the final
+// projection keeps (in_xi in both coordinates, n/2 - 1 per coordinate): slot[pos] is the compact
+// index of permuted position pos, or -1.  Every kernel that reads or writes the compact partials
+// builds the table with this same ascending loop.
+template <int n>
+__host__ __device__ constexpr int xi_kept() {
+  return n / 2 - 1;
+}
+template <int n>
+__device__ __forceinline__ void build_xi_slots(int* slot, int* kept_pos) {
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int pos = 0; pos < n; ++pos) {
+      const bool keep = in_xi<n>(freq_of_pos<n>(pos));
+      slot[pos] = keep ? cnt : -1;
+      if (keep) kept_pos[cnt++] = pos;
+    }
+  }
+  __syncthreads();
+}
+
 // dst = Psi'_j(x) for the field x(i) = ld(i), i = ix * n + iy: row FFT, column convolution with the
 // angle's psi' table, row IFFT (the forward's convolution); G is the staging field.
 template <int n, class C2, class T, class LD>
@@ -347,7 +368,7 @@ __device__ __forceinline__ void psi_conv(C2* sm, const C2* tw, const T* __restri
 // Persistent blocks over units (cell, j, m-chunk); per unit outputs a real
 // partial [2][P] and a spectral partial [2][P].
 // Several cotangents (K of them, mu3 / part_r / part_s of cotangent k at
-// offsets k * mu_stride and k * part_stride) share the shifted fields and the
+// offsets k * mu_stride, k * part_stride and k * spart_stride) share the shifted fields and the
 // T transforms, which depend on the state only: per (j, m) 8 + 8 K
 // convolutions instead of 16 K.
 // --------------------------------------------------------------------------
@@ -357,13 +378,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
     const typename Vec2Of<T>::type* mu3, typename Vec2Of<T>::type* part_r, typename Vec2Of<T>::type* part_s,
     typename Vec2Of<T>::type* ws, const typename Vec2Of<T>::type* __restrict__ gtw,
     const T* __restrict__ psip_s, const typename Vec2Of<T>::type* __restrict__ phase, int J, int M, int nmc, int mch,
-    int nunits, int K, size_t mu_stride, size_t part_stride) {
+    int nunits, int K, size_t mu_stride, size_t part_stride, size_t spart_stride) {
   using C2 = typename Vec2Of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
   C2* sm = tw + n;
   __shared__ int xcols[n];
   __shared__ unsigned char xmask[n];
+  __shared__ int kslot[n];
+  __shared__ int kcols[n];
+  constexpr int NQ = xi_kept<n>(), Q = NQ * NQ;
+  build_xi_slots<n>(kslot, kcols);
   if (threadIdx.x == 0) {
     int cnt = 0;
     for (int pos = 0; pos < n; ++pos) {
@@ -387,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
     const int mc = unit % nmc;
     for (int k = 0; k < K; ++k) {
       zero_fields(part_r + k * part_stride + (size_t)unit * 2 * P, 2 * P);
-      zero_fields(part_s + k * part_stride + (size_t)unit * 2 * P, 2 * P);
+      zero_fields(part_s + k * spart_stride + (size_t)unit * 2 * Q, 2 * Q);
     }
     const T* psp = psip_s + (size_t)j * P;
     const C2* wf = wfine + (size_t)c * 2 * P;
@@ -462,23 +487,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
           __syncthreads();
         }
       }
-      // S^T: forward FFT of the XZ pairs, times the conjugate phase, accumulate in Fourier space
+      // S^T: forward FFT of the XZ pairs, times the conjugate phase, accumulated in Fourier space on
+      // the kept frequencies only (column transforms of the kept columns only)
       for (int k = 0; k < K; ++k) {
         for (int p = 0; p < 2; ++p) {
           const C2* src = XZall + (size_t)(2 * k + p) * P;
-          C2* dst = part_s + k * part_stride + (size_t)unit * 2 * P + (size_t)p * P;
+          C2* dst = part_s + k * spart_stride + (size_t)unit * 2 * Q + (size_t)p * Q;
           row_pass<n, -1, false, 0>(
               sm, tw, [&](int ix, int iy) { return src[ix * n + iy]; }, NoMid(),
               [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
-          col_pass<n, -1, false, 0>(
-              sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
+          col_pass_list<n, -1, false, 0>(
+              sm, tw, kcols, NQ, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
               [&](int ix, int iy, C2 v) {
+                const int sx = kslot[ix];
+                if (sx < 0) return;
                 const C2 ph = cmul(px[ix], py[iy]);
                 const C2 z = cmulc(v, ph);
-                C2 d = dst[ix * n + iy];
+                C2* o = dst + sx * NQ + kslot[iy];
+                C2 d = *o;
                 d.x += z.x;
                 d.y += z.y;
-                dst[ix * n + iy] = d;
+                *o = d;
               });
         }
       }
@@ -499,7 +528,7 @@ template <int n>
 __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
     const float2* what, const float2* wfine, const float2* mu3, float2* part_r, float2* part_s, float2* ws,
     const float2* __restrict__ gtw, const float* __restrict__ psip_s, const float2* __restrict__ phase, int J, int M,
-    int nmc, int mch, int nunits, int K, size_t mu_stride, size_t part_stride) {
+    int nmc, int mch, int nunits, int K, size_t mu_stride, size_t part_stride, size_t spart_stride) {
   using C2 = float2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
@@ -508,10 +537,14 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
   constexpr int LS = n + 1, P = n * n;
   constexpr int kIter = (P + kThreadsI3Smem - 1) / kThreadsI3Smem;
   __shared__ unsigned char xmask[n];
+  __shared__ int kslot[n];
+  __shared__ int kcols[n];
+  constexpr int NQ = xi_kept<n>(), Q = NQ * NQ;
   for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
     const int k = freq_of_pos<n>(pos);
     xmask[pos] = ((k < n / 4) || (k >= n - n / 4)) ? 1 : 0;
   }
+  build_xi_slots<n>(kslot, kcols);
   load_twiddles<n>(tw, gtw);
   C2* slot = ws + (size_t)blockIdx.x * (2 + 2 * K) * P;
   C2* Sig = slot;            // [2]
@@ -522,7 +555,7 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
     const int mc = unit % nmc;
     for (int k = 0; k < K; ++k) {
       zero_fields(part_r + k * part_stride + (size_t)unit * 2 * P, 2 * P);
-      zero_fields(part_s + k * part_stride + (size_t)unit * 2 * P, 2 * P);
+      zero_fields(part_s + k * spart_stride + (size_t)unit * 2 * Q, 2 * Q);
     }
     {
       const float4* src = reinterpret_cast<const float4*>(psip_s + (size_t)j * P);
@@ -620,18 +653,19 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
       for (int kc = 0; kc < K; ++kc) {
         for (int p = 0; p < 2; ++p) {
           const C2* src = XZall + (size_t)(2 * kc + p) * P;
-          C2* dst = part_s + kc * part_stride + (size_t)unit * 2 * P + (size_t)p * P;
+          C2* dst = part_s + kc * spart_stride + (size_t)unit * 2 * Q + (size_t)p * Q;
           for (int idx = threadIdx.x; idx < P; idx += blockDim.x) G[(idx / n) * LS + idx % n] = src[idx];
           __syncthreads();
           fft_lines<n, -1>(G, n, LS, 1, tw);    // rows
           fft_lines<n, -1>(G, n, 1, LS, tw);    // columns
-          for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
-            const int ix = idx / n, iy = idx % n;
+          // accumulated on the kept frequencies only
+          for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+            const int ix = kcols[q / NQ], iy = kcols[q % NQ];
             const C2 z = cmulc(G[ix * LS + iy], cmul(px[ix], py[iy]));
-            C2 d = dst[idx];
+            C2 d = dst[q];
             d.x += z.x;
             d.y += z.y;
-            dst[idx] = d;
+            dst[q] = d;
           }
           __syncthreads();
         }
@@ -642,7 +676,9 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
 
 // --------------------------------------------------------------------------
 // Final: nu = direct + I1 + I2/I4 + 2 nu_f (into w0) + sum of the I3 real
-// partials + IFFT(sum of the I3 spectral partials / n^2); gradient = 4 E P nu.
+// partials; gradient = 4 E P (nu + IFFT(H) / n^2) with H the sum of the I3
+// spectral partials.  P keeps the kept frequencies only and FFT(IFFT(H)) =
+// n^2 H, so H (stored on those frequencies) is added to FFT(nu) there.
 // One block per cell; writes grad[c][4][N][N] (FP64).
 // --------------------------------------------------------------------------
 template <int n, class T>
@@ -654,57 +690,60 @@ __global__ void __launch_bounds__(kThreads) k_vjp_final(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
   C2* sm = tw + n;
+  __shared__ int kslot[n];
+  __shared__ int kcols[n];
+  build_xi_slots<n>(kslot, kcols);
   load_twiddles<n>(tw, gtw);
   constexpr int N = n / 2, P = n * n;
+  constexpr int NQ = xi_kept<n>(), Q = NQ * NQ;
   const int c = blockIdx.x;
-  C2* slot = ws + (size_t)blockIdx.x * 4 * P;
-  C2* V = slot;            // [2] total cotangent pairs
-  C2* H = slot + 2 * P;    // [2] spectral sum
+  C2* slot = ws + (size_t)blockIdx.x * 5 * P;
+  C2* V = slot;            // [2] total real-space cotangent pairs
+  C2* F = slot + 2 * P;    // [2] their transforms
+  C2* H = slot + 4 * P;    // [2][Q] spectral sum on the kept frequencies
   const C2* pr = part_r + (size_t)c * nparts * 2 * P;
-  const C2* ps = part_s + (size_t)c * nparts * 2 * P;
+  const C2* ps = part_s + (size_t)c * nparts * 2 * Q;
   for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) {
-    double sx = 0, sy = 0, hx = 0, hy = 0;
+    double sx = 0, sy = 0;
     for (int u = 0; u < nparts; ++u) {
-      const C2 a = pr[(size_t)u * 2 * P + i], b = ps[(size_t)u * 2 * P + i];
-      sx += (double)a.x; sy += (double)a.y; hx += (double)b.x; hy += (double)b.y;
+      const C2 a = pr[(size_t)u * 2 * P + i];
+      sx += (double)a.x; sy += (double)a.y;
     }
     const C2 d = nu[(size_t)c * 2 * P + i];
     double vx = (double)d.x + sx, vy = (double)d.y + sy;
     if (i < P) vx += 2.0 * (double)nuf[(size_t)c * P + i];
     V[i] = mk2((T)vx, (T)vy);
+  }
+  for (int i = threadIdx.x; i < 2 * Q; i += blockDim.x) {
+    double hx = 0, hy = 0;
+    for (int u = 0; u < nparts; ++u) {
+      const C2 b = ps[(size_t)u * 2 * Q + i];
+      hx += (double)b.x; hy += (double)b.y;
+    }
     H[i] = mk2((T)hx, (T)hy);
   }
   __syncthreads();
   const T invP = (T)(1.0 / (double)P);
   for (int p = 0; p < 2; ++p) {
     C2* Vp = V + (size_t)p * P;
-    C2* Hp = H + (size_t)p * P;
-    // spectral partials (permuted order) back to real space, added to V
-    col_pass<n, 1, false, 0>(
-        sm, tw, [&](int ix, int iy) { return Hp[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, C2 v) { Hp[ix * n + iy] = v; });
-    row_pass<n, 1, false, 0>(
-        sm, tw, [&](int ix, int iy) { return Hp[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, C2 v) {
-          C2 o = Vp[ix * n + iy];
-          o.x += v.x * invP;
-          o.y += v.y * invP;
-          Vp[ix * n + iy] = o;
-        });
-    // 4 E P V
+    C2* Fp = F + (size_t)p * P;
+    const C2* Hp = H + (size_t)p * Q;
+    // 4 E P (V + IFFT(H) / n^2)
     row_pass<n, -1, false, 0>(
         sm, tw, [&](int ix, int iy) { return Vp[ix * n + iy]; }, NoMid(),
-        [&](int ix, int iy, C2 v) { Hp[ix * n + iy] = v; });
+        [&](int ix, int iy, C2 v) { Fp[ix * n + iy] = v; });
     col_pass<n, -1, true, 1>(
-        sm, tw, [&](int ix, int iy) { return Hp[ix * n + iy]; },
+        sm, tw, [&](int ix, int iy) { return Fp[ix * n + iy]; },
         [&](int ix, int iy, C2 v) {
-          const bool keep = in_xi<n>(freq_of_pos<n>(ix)) && in_xi<n>(freq_of_pos<n>(iy));
-          return keep ? cscale(v, invP) : zero2<T>();
+          const int sx = kslot[ix], sy = kslot[iy];
+          if (sx < 0 || sy < 0) return zero2<T>();
+          const C2 h = Hp[sx * NQ + sy];
+          return cscale(cadd(v, h), invP);
         },
-        [&](int ix, int iy, C2 v) { Hp[ix * n + iy] = v; });
+        [&](int ix, int iy, C2 v) { Fp[ix * n + iy] = v; });
     double* g = grad + (size_t)c * 4 * N * N;
     row_pass<n, 1, false, 0>(
-        sm, tw, [&](int ix, int iy) { return Hp[ix * n + iy]; }, NoMid(),
+        sm, tw, [&](int ix, int iy) { return Fp[ix * n + iy]; }, NoMid(),
         [&](int ix, int iy, C2 v) {
           if (((ix | iy) & 1) == 0) {
             const int i = ix >> 1, j = iy >> 1;
@@ -756,6 +795,7 @@ cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const
   const size_t r_stride = (size_t)vw.nb * P;               // real cotangent buffers, per cotangent
   const size_t nparts = (size_t)vw.nb * t.J * vw.nmc;
   const size_t part_stride = nparts * 2 * P;
+  const size_t spart_stride = nparts * 2 * (size_t)xi_kept<n>() * xi_kept<n>();
   auto begin = [&](int g) { if (tm) tm->begin(g, s); };
   auto end = [&]() { if (tm) tm->end(s); };
   begin(KG_VJP);
@@ -783,17 +823,17 @@ cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     k_i3_vjp_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(
         what, wfine, (C2*)vw.mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M, vw.nmc,
-        vw.mch, nunits, K, c_stride, part_stride);
+        vw.mch, nunits, K, c_stride, part_stride, spart_stride);
   else
     k_i3_vjp<n, T><<<grid, kThreads, sm, s>>>(what, wfine, (C2*)vw.mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw,
                                               tb.psip_s, tb.phase, t.J, t.M, vw.nmc, vw.mch, nunits, K, c_stride,
-                                              part_stride);
+                                              part_stride, spart_stride);
   end();
   ++launches;
   begin(KG_VJP);
   for (int k = 0; k < K; ++k) {
     k_vjp_final<n, T><<<ncells, kThreads, sm, s>>>((C2*)vw.nu + k * c_stride, (T*)vw.nuf + k * r_stride,
-                                                   (C2*)vw.part_r + k * part_stride, (C2*)vw.part_s + k * part_stride,
+                                                   (C2*)vw.part_r + k * part_stride, (C2*)vw.part_s + k * spart_stride,
                                                    t.J * vw.nmc, ws, tb.tw, grad[k], accumulate);
     ++launches;
   }

@@ -113,7 +113,7 @@ struct VjpWork {
   void* mu4 = nullptr;   // [nb][2][n*n] cotangent of the raw K4 pairs
   void* mu3 = nullptr;   // [nb][2][n*n] cotangent of the raw K3 pairs
   void* part_r = nullptr;  // [nb*J*nmc][2][n*n] I3 transpose partials, real space
-  void* part_s = nullptr;  // [nb*J*nmc][2][n*n] I3 transpose partials, Fourier space
+  void* part_s = nullptr;  // [nb*J*nmc][2][(n/2-1)^2] I3 transpose partials, Fourier space, kept frequencies
   void* ws = nullptr;
 };
 
