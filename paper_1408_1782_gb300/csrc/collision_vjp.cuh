@@ -366,7 +366,8 @@ __device__ __forceinline__ void psi_conv(C2* sm, const C2* tw, const T* __restri
 // (i) and (iii) are summed before one forward FFT and accumulated in Fourier
 // space with the conjugate phase; (ii) is accumulated in real space.
 // Persistent blocks over units (cell, j, m-chunk); per unit outputs a real
-// partial [2][P] and a spectral partial [2][P].
+// partial [2][P] and a spectral partial [2][Q] on the kept frequencies
+// (Q = (n/2 - 1)^2, see build_xi_slots).
 // Several cotangents (K of them, mu3 / part_r / part_s of cotangent k at
 // offsets k * mu_stride, k * part_stride and k * spart_stride) share the shifted fields and the
 // T transforms, which depend on the state only: per (j, m) 8 + 8 K
