@@ -460,3 +460,78 @@ def test_rk2_substep_second_order_on_pure_precession():
         errs.append(np.abs(W[:, 1:, 1, 2] - exact).max())
         assert np.abs(W[:, 0] - 0.5).max() < 1e-13
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+# --------------------------------------------------------------------------
+# Sub-cycled transport A(tau) and the split step (Sec. 4, eq. slopeLimiterStep)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [2, 3])
+def test_advect_subcycles_in_equal_unit_courant_steps(s):
+    """A(tau) with tau = s dx/L takes s sub-steps of tau/s: on the row v_x = -L each has
+    |nu| = 1, where eq. slopeLimiterStep is an exact shift by one cell (Godunov moves the
+    whole cell, the limiter factor (sgn nu - nu)/2 vanishes).  A(tau) is then a shift by s
+    cells; sub-steps of length tau (|nu| = s) or a wrong count give something else."""
+    p = O.Params(N=8)
+    Nx = 10
+    dx = 1.0 / Nx
+    W = np.random.default_rng(20 + s).uniform(0, 1, size=(Nx, 4, 8, 8))
+    out = O.advect(W, s * dx / p.L, p, O.Boundary("periodic"))
+    assert np.abs(out[:, :, 0, :] - np.roll(W, -s, axis=0)[:, :, 0, :]).max() < 1e-14
+
+
+def test_advect_subcycles_match_textbook_flux_form():
+    """A(tau) with tau = 1.5 dx/L: two sub-steps of Courant number -0.75 (max |v_x| = L) on
+    the row v_x = -L, and two of -0.75 |v_x|/L on the others; each is LeVeque's flux-form
+    minmod step (written out independently in this file)."""
+    p = O.Params(N=8)
+    Nx = 12
+    dx = 1.0 / Nx
+    W = np.random.default_rng(31).normal(size=(Nx, 4, 8, 8))
+    out = O.advect(W, 1.5 * dx / p.L, p, O.Boundary("periodic"))
+    vx, _ = O.velocity_nodes(p)
+    for ix in range(8):
+        nu = 0.75 * vx[ix, 0] / p.L
+        for c in (0, 3):
+            u = W[:, c, ix, 5]
+            ref = _flux_form_limiter_step(_flux_form_limiter_step(u, nu), nu)
+            assert np.abs(out[:, c, ix, 5] - ref).max() < 1e-13
+
+
+def _heun_linear(A, dt):
+    """Heun's method on w' = A w is exactly w -> (1 + dt A + dt^2 A^2 / 2) w."""
+    return np.eye(A.shape[0]) + dt * A + 0.5 * dt * dt * A @ A
+
+
+def test_step_is_half_transport_collision_half_transport():
+    """step = A(dt/2) o RK2(dt) o A(dt/2) (Sec. 4).  With dt/2 = dx/L every half step shifts
+    the row v_x = -L by exactly one cell.  w0 = 1/2 makes C_c and the I4 term vanish and a
+    truncation radius R = 1e-6 makes the rest O(R^2), so the substep is Heun on the
+    precession w' = 2 B(x) x w, a linear map per cell.  Along the row the step must give
+    out_i = H(B_{i+1}) W_{i+2}: collision placed first or last would use B_{i+2} or B_i,
+    full-length transport steps would shift by four cells."""
+    p = O.Params(N=4, R=1e-6, J=2, M=1)
+    Nx = 8
+    dx = 1.0 / Nx
+    dt = 2.0 * dx / p.L
+    rng = np.random.default_rng(44)
+    x = (np.arange(Nx) + 0.5) / Nx
+    W = np.zeros((Nx, 4, 4, 4))
+    W[:, 0] = 0.5
+    W[:, 1:] = 0.3 * np.stack([np.cos(2 * np.pi * x), np.sin(4 * np.pi * x), np.cos(6 * np.pi * x + 1)], -1)[:, :, None, None]
+    W += 0.05 * rng.normal(size=W.shape) * np.array([0, 1, 1, 1])[None, :, None, None]
+    bc = O.Boundary("periodic")
+    out0 = O.step(W, np.zeros((Nx, 3)), dt, p, bc)
+    assert np.abs(out0[:, :, 0, :] - np.roll(W, -2, axis=0)[:, :, 0, :]).max() < 1e-10
+    B = np.stack([1.5 * np.sin(2 * np.pi * x), 0.8 + np.cos(2 * np.pi * x), -np.cos(4 * np.pi * x)], -1)
+    out = O.step(W, B, dt, p, bc)
+    for i in range(Nx):
+        b = B[(i + 1) % Nx]
+        A = 2.0 * np.array([[0, -b[2], b[1]], [b[2], 0, -b[0]], [-b[1], b[0], 0]])   # w -> 2 b x w
+        ref = _heun_linear(A, dt) @ W[(i + 2) % Nx, 1:, 0, :]
+        assert np.abs(out[i, 1:, 0, :] - ref).max() < 1e-10
+        assert np.abs(out[i, 0, 0, :] - 0.5).max() < 1e-12
+        wrong = _heun_linear(A, dt) @ W[(i + 2) % Nx, 1:, 0, :] - _heun_linear(
+            2.0 * np.array([[0, -B[i][2], B[i][1]], [B[i][2], 0, -B[i][0]], [-B[i][1], B[i][0], 0]]), dt
+        ) @ W[(i + 2) % Nx, 1:, 0, :]
+        assert np.abs(wrong).max() > 1e-4          # the placements are distinguishable
