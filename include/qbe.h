@@ -339,10 +339,13 @@ int qbe_batch_step(qbe_batch* b, double dt, int nsteps);
  * Memory: no cudaMalloc, no cudaFree, no host heap.  Kernel tables and every
  * piece of scratch live in one statically sized device array of
  * QBE_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds until
- * the process exits.  The first call on a device resolves that array's address
- * (cudaGetSymbolAddress) and every call whose grid (N, J, M, L, R) differs
- * from the previous call's rebuilds the tables in the array with two extra
- * kernel launches; make that first call before any stream capture.  Cells are
+ * the process exits.  Every call resolves that array's address
+ * (cudaGetSymbolAddress, which allocates nothing) and a call whose grid
+ * (N, J, M, L, R) differs from the previous call's rebuilds the tables in the
+ * array with two extra kernel launches; make the first call on a device before
+ * any stream capture.  A call issued while its stream is being captured always
+ * records the rebuild, and every later call on that device rebuilds too (the
+ * host can no longer tell which grid the array holds).  Cells are
  * processed in batches that fit the array.  Every call shares the array and
  * leaves its contents behind; the kernels initialise everything they read, so
  * no clearing is needed between calls, but calls that overlap on the GPU (on

@@ -25,10 +25,12 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 struct DeviceSlot {
-  bool ready = false;           // symbol address resolved on this device
-  unsigned char* base = nullptr;
-  // grid whose tables the array currently holds
+  unsigned char* base = nullptr;  // the array's device address on this device, as last resolved
+  // grid whose tables the array currently holds (as far as the host can know)
   bool tables = false;
+  // a call was recorded into a stream capture: the array's contents then depend on when that
+  // graph is replayed, so every later call rebuilds the tables
+  bool captured = false;
   int N = 0, J = 0, M = 0;
   double L = 0, R = 0;
 };
@@ -193,9 +195,9 @@ extern "C" int qbe_collide_noalloc(const qbe_grid* g, const double* w, double* c
            align256(wsf * P * sizeof(double2));
   };
   // largest batch (<= ncells) and I3 grid that fit
-  int nb = ncells, grid = 0;
+  int nb = ncells < (1 << 20) ? ncells : (1 << 20), grid = 0;
   for (;;) {
-    grid = nb * g->J < nsm ? nb * g->J : nsm;
+    grid = (long long)nb * g->J < nsm ? nb * g->J : nsm;
     if (need(nb, grid) <= kScratchBytes || nb == 1) break;
     nb = nb / 2 > 0 ? nb / 2 : 1;
   }
@@ -203,15 +205,21 @@ extern "C" int qbe_collide_noalloc(const qbe_grid* g, const double* w, double* c
   if (need(nb, grid) > kScratchBytes) return QBE_ERR_ARG;   // grid too large for the static scratch
 
   DeviceSlot& slot = g_slots[dev];
-  if (!slot.ready) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return QBE_ERR_CUDA;
-    slot.base = (unsigned char*)p;
-    slot.ready = true;
+  // Resolved on every call (it allocates nothing): a new context may place the array elsewhere.
+  void* sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_noalloc_scratch) != cudaSuccess || !sym) return QBE_ERR_CUDA;
+  if ((unsigned char*)sym != slot.base) {
+    slot.base = (unsigned char*)sym;
+    slot.tables = false;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return QBE_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) slot.captured = true;
   unsigned char* base = slot.base;
-  if (!slot.tables || slot.N != g->N || slot.J != g->J || slot.M != g->M || slot.L != g->L || slot.R != g->R) {
+  if (slot.captured || !slot.tables || slot.N != g->N || slot.J != g->J || slot.M != g->M || slot.L != g->L ||
+      slot.R != g->R) {
+    slot.tables = false;          // the build below overwrites the table area
     cudaError_t e;
     switch (n) {
       case 16: e = build_tables_dev<16>(base, lay, g->J, g->M, g->L, g->R, s); break;

@@ -75,3 +75,29 @@ def test_noalloc_rejects_what_does_not_fit(qbe):
     g = qbe.QbeGrid(128, 1, 8, 8, 12.0, 7.5, 0, torch.cuda.current_device())     # N = 128 unsupported
     assert qbe.lib().qbe_collide_noalloc(ctypes.byref(g), ctypes.c_void_p(w.data_ptr()),
                                          ctypes.c_void_p(out.data_ptr()), 1, None) == -1
+
+
+def test_noalloc_allocates_no_device_memory(qbe):
+    """The property the entry point exists for: once its kernels are loaded (first calls on
+    both grids), further calls -- with a grid change, which rebuilds the tables, and without
+    one -- leave the device's free memory exactly where it was."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    wa = torch.from_numpy(inputs.synthetic_w(16, 3, seed=5)).cuda()
+    wb = torch.from_numpy(inputs.synthetic_w(32, 2, seed=6)).cuda()
+    oa, ob = torch.empty_like(wa), torch.empty_like(wb)
+    for w, o in ((wa, oa), (wb, ob)):
+        qbe.collide_noalloc(w, o, J=8, M=6, stream=stream)
+    torch.cuda.synchronize()
+    first = oa.cpu().numpy()
+    free0, _ = torch.cuda.mem_get_info()
+    qbe.collide_noalloc(wa, oa, J=8, M=6, stream=stream)     # grid change: tables rebuilt
+    qbe.collide_noalloc(wa, oa, J=8, M=6, stream=stream)     # same grid
+    qbe.collide_noalloc(wb, ob, J=8, M=6, stream=stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    qbe.collide_noalloc(wa, oa, J=8, M=6, stream=stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(oa.cpu().numpy(), first)
