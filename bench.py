@@ -8,7 +8,12 @@ Fermi-Dirac-perturbed state (5 % Hermitian perturbation).  One step = one
 split time step of all 128 cells = 2 collision-operator evaluations.
 
 Prints one JSON line (rank 0).  Metric: C[W] cell*k-pts/s
-(= 2 * Nx * N^2 collision evaluations per step / time).
+(= 2 * Nx * N^2 collision evaluations per step / time).  At N = 1 the line's
+"forms" object carries the rest of the metric on the same 64 x 64, Nx = 128
+grid: the FP32-split form of the workload (steps/s, C[W] cell*k-pts/s, its
+error against the FP64 GPU form and the stored oracle cells, stated
+tolerances) and the adjoint/forward time ratio of the differentiation
+configuration over a short horizon (--forms-horizon, default 2 split steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --mode collide [--cells C]   # time C[W] alone on the first C cells
@@ -121,7 +126,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Fermi-Dirac-perturbed W)", "impl_note": "FP64 CPU oracle",
-        "config": config_dict(wl, args.gpus, reference=True),
+        "config": config_dict(wl, args.gpus),
+        "runs_on": f"host cores ({cores} spawned processes); rank 0 only",
         "cpu_baseline": {"value": value, "unit": "cell·k-pts/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "cell·k-pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -129,7 +135,8 @@ def run_reference(args):
     return 0
 
 
-def config_dict(wl, ngpu, reference=False):
+def config_dict(wl, ngpu):
+    """The workload's description; identical for both arms (where each arm runs is stated outside it)."""
     walls = {"dirichlet": "Dirichlet walls (Fermi-Dirac beta=1, mu=0)",
              "maxwell": f"Maxwell walls (alpha={wl.get('alpha', 0)}, Fermi-Dirac beta=1, mu=0)",
              "periodic": "periodic"}[wl["bc"]]
@@ -140,9 +147,9 @@ def config_dict(wl, ngpu, reference=False):
                      f"{int(100 * wl['perturb'])}% perturbed synthetic W"),
         "N": wl["N"], "Nx": wl["Nx"], "J": wl["J"], "M": wl["M"], "dt": wl["dt"],
         "bc": wl["bc"], "B": list(wl["B"]), "precision": "f64" if wl.get("precision", 0) == 0 else "f32-split",
-        "l2": ("not applicable (host cores)" if reference else
-               "256 MiB buffer zeroed before every timed step (working set also exceeds L2)"),
-        "parallelism": "oracle on host cores" if reference else ("single GPU" if ngpu == 1 else f"{ngpu} replicas"),
+        "l2": ("GPU arm: 256 MiB buffer zeroed before every timed step (working set also exceeds L2); "
+               "reference arm (host cores): no flush"),
+        "parallelism": "single GPU" if ngpu == 1 else f"{ngpu} replicas",
     }
 
 
@@ -198,6 +205,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_sm_max():
+    try:
+        return float(json.load(open(MEASURED_PEAKS)).get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 2070.0
+
+
+def gpu_uuid(local):
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -249,13 +273,7 @@ def run_ours(args):
         s.step(wl["dt"], 1)
     torch.cuda.synchronize()
 
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(local).uuid)
-        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    except Exception:
-        uuid = None
-    clocks = ClockSampler(uuid)
+    clocks = ClockSampler(gpu_uuid(local))
     s.enable_timing(True)
     launches0 = s.launch_count()
     clocks.start()
@@ -301,11 +319,7 @@ def run_ours(args):
     avg_i3_s = i3["ms"] * 1e-3 / max(i3["launches"], 1)
     flops_per_launch = Nx * wl["J"] * wl["M"] * i3_flops_per_unit(N)
     achieved = flops_per_launch / avg_i3_s / 1e12
-    sm_max = 2070.0
-    try:
-        sm_max = float(json.load(open(MEASURED_PEAKS)).get("sm_max_mhz", sm_max))
-    except Exception:
-        pass
+    sm_max = measured_sm_max()
     lanes = FP64_FMA_PER_CLK_PER_SM if prec == 0 else FP32_FMA_PER_CLK_PER_SM
     peak = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
     total_group_ms = sum(v["ms"] for v in groups.values())
@@ -340,6 +354,9 @@ def run_ours(args):
     precision_report = None
     if prec == 1 and rank == 0:
         precision_report = fp32_split_report(wl, W0, local, qbe, torch, np)
+    forms = None
+    if args.workload == "plain_fp64_n64" and world == 1 and not args.no_forms:
+        forms = measure_forms(args, wl, W0, s, t_ms / args.steps, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -377,11 +394,114 @@ def run_ours(args):
         }
         if precision_report is not None:
             line["precision_report"] = precision_report
+        if forms is not None:
+            line["forms"] = forms
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_forms(args, wl, W0, s64, fp64_ms_per_step, local):
+    """The rest of the benchmark metric on the same N = 64, Nx = 128 grid: the FP32-split form of
+    this workload (steps/s and C[W] cell*k-pts/s with its error against the plain FP64 GPU form and
+    the stored oracle cells) and the adjoint/forward ratio of the differentiation configuration
+    (periodic, FP32-split) over a short horizon."""
+    import numpy as np
+    import torch
+
+    from paper_1408_1782_gb300 import inputs, qbe
+
+    N, Nx = wl["N"], wl["Nx"]
+    stream = torch.cuda.current_stream()
+    s = qbe.Solver(N, Nx, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream, precision=1)
+    fd = qbe.fd_state(wl["wall"]["beta"], wl["wall"]["mu_up"], wl["wall"]["mu_dn"])
+    s.set_boundary(wl["bc"], fd, fd, alpha=wl.get("alpha", 0.0))
+    s.set_bfield(inputs.uniform_b(Nx, wl["B"]))
+    s.set_state(W0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        s.step(wl["dt"], 1)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 5)
+    sampler = ClockSampler(gpu_uuid(local))
+    s.enable_timing(True)
+    launches0 = s.launch_count()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        flush.zero_()
+        s.step(wl["dt"], 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = sampler.stop()
+    t_ms = e0.elapsed_time(e1)
+    launches = s.launch_count() - launches0
+    i3_ms, i3_n = s.kernel_time("i3")
+    s.enable_timing(False)
+    units = 2 * Nx * N * N
+    # end to end: the state in from pinned host memory and out again around each step
+    host = torch.from_numpy(W0).pin_memory()
+    host_out = torch.empty_like(host).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(steps, args.e2e_steps))
+    for _ in range(e2e_steps):
+        s.set_state(host)
+        s.step(wl["dt"], 1)
+        s.get_state(host_out)
+    t_e2e = time.perf_counter() - t0
+    # error of C[W] at the initial state: every cell against the FP64 GPU form, and the stored
+    # oracle cells of this workload
+    w = torch.from_numpy(W0).cuda()
+    c32 = s.collide(w).cpu().numpy()
+    c64 = s64.collide(w).cpu().numpy()
+    paper_norm = lambda a, b: float(max(sum(np.abs(a[i, k] - b[i, k]).sum() / np.abs(b[i, k]).sum()
+                                            for k in range(4)) for i in range(a.shape[0])))
+    err = {"max_rel_vs_fp64_gpu": float(np.abs(c32 - c64).max() / np.abs(c64).max()),
+           "paper_norm_vs_fp64_gpu": paper_norm(c32, c64), "cells_compared_with_fp64_gpu": Nx}
+    gold = os.path.join(ROOT, "tests", "golden", "plain_fp64_n64_cells.npz")
+    if os.path.exists(gold):
+        g = np.load(gold)
+        cg = c32[g["cells"]]
+        err["max_rel_vs_oracle_cells"] = float(np.abs(cg - g["C"]).max() / np.abs(g["C"]).max())
+        err["paper_norm_vs_oracle_cells"] = paper_norm(cg, g["C"])
+        err["oracle_cells"] = [int(c) for c in g["cells"]]
+    err["tolerance_max_rel"] = 5e-6
+    err["tolerance_paper_norm"] = 5e-5
+    err["within_tolerance"] = bool(err["max_rel_vs_fp64_gpu"] < 5e-6 and err["paper_norm_vs_fp64_gpu"] < 5e-5 and
+                                   err.get("max_rel_vs_oracle_cells", 0) < 5e-6 and
+                                   err.get("paper_norm_vs_oracle_cells", 0) < 5e-5)
+    sm_max = measured_sm_max()
+    peak32 = SM_COUNT * FP32_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+    avg_i3 = i3_ms * 1e-3 / max(i3_n, 1)
+    achieved = Nx * wl["J"] * wl["M"] * i3_flops_per_unit(N) / avg_i3 / 1e12
+    fp32 = {
+        "form": "FP32-split: collision transforms and products in FP32; input, output, partial-sum reduction, "
+                "transport, RK2 and moments in FP64",
+        "metric": "C[W] cell·k-pts/s", "value": steps * units / (t_ms * 1e-3), "unit": "cell·k-pts/s",
+        "steps": steps, "warmup": args.warmup, "ms_per_step": t_ms / steps, "steps_per_s": 1e3 * steps / t_ms,
+        "speedup_vs_fp64_gpu_step": fp64_ms_per_step / (t_ms / steps),
+        "error": err,
+        "roofline": {"kernel": "k_i3_smem (Hu-Ying I3 term, FP32)", "bound": "alu", "achieved": achieved,
+                     "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
+                     "avg_launch_ms": avg_i3 * 1e3,
+                     "peak_source": f"derived: {SM_COUNT} SMs x {FP32_FMA_PER_CLK_PER_SM} FP32 FMA/clk x 2 flop x "
+                                    f"{sm_max:.0f} MHz"},
+        "e2e": {"value": e2e_steps * units / t_e2e, "unit": "cell·k-pts/s", "h2d_bytes_per_step": W0.nbytes,
+                "d2h_bytes_per_step": W0.nbytes, "steps": e2e_steps},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    s.close()
+    awl = workload("adjoint_n64")
+    H, every = args.forms_horizon, 1
+    adj = measure_adjoint(awl, local, H, every, steps=2, warmup=1, cpu_baseline=False, clocks=True)
+    adj["note"] = (f"the differentiation configuration (N=64, Nx=128, periodic, B=(0.3,0,0.4), FP32-split) "
+                   f"over {H} split steps with a checkpoint every step; the per-step ratio does not depend on "
+                   f"the horizon (each segment is recomputed once from its checkpoint)")
+    return {"fp32_split": fp32, "adjoint": adj}
 
 
 def fp32_split_report(wl, W0, local, qbe, torch, np):
@@ -549,18 +669,32 @@ def run_adjoint(args, local):
     initial state W_0 and the field B: forward sweep (qbe_step_checkpointed over the horizon) and
     reverse sweep (qbe_observables_vjp + qbe_step_vjp).  One timed step = one gradient of both
     observables (one forward sweep, one reverse sweep carrying both cotangents)."""
+    wl = workload("adjoint_n64", args.precision)
+    H = args.horizon or wl["checkpoint_every"]
+    every = min(wl["checkpoint_every"], H)
+    line = measure_adjoint(wl, local, H, every, args.steps, args.warmup,
+                           cpu_baseline=not args.no_cpu_baseline, clocks=True)
+    line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "scaling": "weak", "vs_baseline": None,
+                 "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)"})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clocks=True):
+    """Time `steps` gradients of (P_z, Phi_E) after H split steps of the workload `wl` (checkpoint
+    every `every`); returns the adjoint/forward ratio with its roofline, e2e and kernel times."""
     import numpy as np
     import torch
 
     from paper_1408_1782_gb300 import inputs, qbe
 
-    wl = workload("adjoint_n64", args.precision)
     N, Nx, prec = wl["N"], wl["Nx"], wl.get("precision", 0)
-    H = args.horizon or wl["checkpoint_every"]
-    every = min(wl["checkpoint_every"], H)
     stream = torch.cuda.current_stream()
     s = qbe.Solver(N, Nx, J=wl["J"], M=wl["M"], L=wl["L"], R=wl["R"], device=local, stream=stream,
                    precision=prec)
+    if wl["bc"] != "periodic":
+        fd = qbe.fd_state(wl["wall"]["beta"], wl["wall"]["mu_up"], wl["wall"]["mu_dn"])
+        s.set_boundary(wl["bc"], fd, fd, alpha=wl.get("alpha", 0.0))
     B = torch.from_numpy(inputs.uniform_b(Nx, wl["B"])).cuda()
     W0 = torch.from_numpy(inputs.synthetic_w(N, Nx, L=wl["L"], seed=0, perturb=wl["perturb"])).cuda()
     lams = torch.empty((2,) + tuple(W0.shape), dtype=torch.float64, device="cuda")
@@ -587,28 +721,23 @@ def run_adjoint(args, local):
         if events:
             events[2].record(stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         gradient()
     torch.cuda.synchronize()
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(local).uuid)
-        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    except Exception:
-        uuid = None
-    clocks = ClockSampler(uuid)
+    sampler = ClockSampler(gpu_uuid(local)) if clocks else None
     s.enable_timing(True)
     launches0 = s.launch_count()
-    clocks.start()
+    if sampler:
+        sampler.start()
     fwd, rev = 0.0, 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         e = [ev(), ev(), ev()]
         gradient(e)
         torch.cuda.synchronize()
         fwd += e[0].elapsed_time(e[1])
         rev += e[1].elapsed_time(e[2])
-    clk = clocks.stop()
+    clk = sampler.stop() if sampler else None
     launches = s.launch_count() - launches0
     vi3_ms, vi3_n = s.kernel_time("vjp_i3")
     groups = {gname: s.kernel_time(gname)[0] for gname in qbe.KERNEL_GROUPS}
@@ -618,11 +747,7 @@ def run_adjoint(args, local):
     avg_vi3 = vi3_ms * 1e-3 / max(vi3_n, 1)
     kgrp = vjp_cotangent_group(prec, N, 2)            # the sweep carries two cotangents
     flops = Nx * wl["J"] * wl["M"] * i3_vjp_flops_per_unit(N, kgrp)
-    sm_max = 2070.0
-    try:
-        sm_max = float(json.load(open(MEASURED_PEAKS)).get("sm_max_mhz", sm_max))
-    except Exception:
-        pass
+    sm_max = measured_sm_max()
     lanes = FP64_FMA_PER_CLK_PER_SM if prec == 0 else FP32_FMA_PER_CLK_PER_SM
     peak = SM_COUNT * lanes * 2 * sm_max * 1e6 / 1e12
     achieved = flops / avg_vi3 / 1e12
@@ -643,23 +768,19 @@ def run_adjoint(args, local):
     s.observables_vjp(np.array([1.0, 0.0]), out=hl)
     s.step_vjp(hl, out=hl0, grad_B=hgB)
     t2 = time.perf_counter()
-    cpu = None
-    if not args.no_cpu_baseline:
-        cpu = adjoint_cpu_baseline(wl)
-    conf = config_dict(dict(wl, name="adjoint_n64"), 1)
+    cpu = adjoint_cpu_baseline(wl) if cpu_baseline else None
+    conf = config_dict(wl, 1)
     conf.update({"horizon_steps": H, "checkpoint_every": every,
                  "workload": conf["workload"] + f"; gradient of P_z and Phi_E after {H} split steps "
                                                 f"(checkpoint every {every}) w.r.t. W_0 and B"})
     line = {
         "metric": "adjoint/forward time ratio", "value": ratio,
         "unit": "reverse s per observable gradient (P_z and Phi_E in one sweep) / forward sweep s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": (fwd + rev) / args.steps, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32-split",
-        "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)", "config": conf,
-        "forward_ms_per_split_step": fwd / args.steps / H,
-        "reverse_ms_per_split_step_both_gradients": rev / args.steps / H,
-        "gradients_per_s": 2e3 * args.steps / (fwd + rev),
+        "ms_per_step": (fwd + rev) / steps, "higher_is_better": False,
+        "dtype": "f64" if prec == 0 else "f32-split", "config": conf,
+        "forward_ms_per_split_step": fwd / steps / H,
+        "reverse_ms_per_split_step_both_gradients": rev / steps / H,
+        "gradients_per_s": 2e3 * steps / (fwd + rev),
         "observables": obs.cpu().tolist(),
         "roofline": {"kernel": "k_i3_vjp (transpose of the Hu-Ying I3 term)", "bound": "alu",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -673,11 +794,11 @@ def run_adjoint(args, local):
                 "d2h_bytes_per_step": obs_host.nbytes + hl.numel() * 8 * 2 + hgB.numel() * 8,
                 "note": "one observable's gradient; forward sweep incl. H2D of W_0 and B, reverse incl. D2H"},
         "gpu_launches": launches,
-        "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    if clk is not None:
+        line["clocks"] = clk
     s.close()
-    return 0
+    return line
 
 
 def adjoint_cpu_baseline(wl):
@@ -760,6 +881,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: skip the FP32-split and adjoint measurements of the same grid")
+    ap.add_argument("--forms-horizon", type=int, default=2,
+                    help="split steps of the adjoint measurement inside the default line")
     ap.add_argument("--mode", choices=["step", "collide", "vjp"], default="step")
     ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128", "batched_16", "batched_64",
                                            "adjoint_n64"],

@@ -24,3 +24,8 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+    # the two arms describe the workload with the same config object
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert d["config"] == json.loads(json.dumps(bench.config_dict(bench.workload("plain_fp64_n64"), 1)))
