@@ -152,8 +152,12 @@ def validation_w(N: int, L: float = 12.0) -> np.ndarray:
     return np.stack([w0, w1, w2, w3])
 
 
-def homogeneous_w0(N: int, L: float = 12.0) -> np.ndarray:
-    """Initial state of Sec. 5.2 (eq. W0homogeneous): kT=5/4, mu=(1, 3/2), v0=(0.4,-0.1); [4,N,N]."""
+def homogeneous_w0(N: int, L: float = 12.0, vy_smoothing: float = 0.0, rotation: float = 1.0) -> np.ndarray:
+    """Initial state of Sec. 5.2 (eq. W0homogeneous): kT=5/4, mu=(1, 3/2), v0=(0.4,-0.1); [4,N,N].
+
+    Variants for convergence studies (defaults give the paper's state): ``vy_smoothing`` = e > 0
+    replaces |v_y| in X(v) by sqrt(v_y^2 + e^2) (no kink at v_y = 0); ``rotation`` scales the
+    sigma part of X(v) (0: the Fermi-Dirac state U0 diag(n) U0^+ without v-dependent rotation)."""
     vx, vy = velocity_mesh(N, L)
     c, s = np.cos(np.pi / 5), np.sin(np.pi / 5)
     U0 = np.array([[c, -1j * s], [s, 1j * c]], dtype=np.complex128)
@@ -163,7 +167,8 @@ def homogeneous_w0(N: int, L: float = 12.0) -> np.ndarray:
     D[..., 0, 0] = _fd_occupation(1.0 / kT, e, mus[0])
     D[..., 1, 1] = _fd_occupation(1.0 / kT, e, mus[1])
     # X(v) = sin(vy^2) 1 + (vx-1) s1 + 2/(vx^2+|vy|+1) s2 + cos(vx + vy/2) s3
-    xvec = np.stack([vx - 1.0, 2.0 / (vx**2 + np.abs(vy) + 1.0), np.cos(vx + 0.5 * vy)], axis=-1)
+    ay = np.abs(vy) if vy_smoothing <= 0.0 else np.sqrt(vy**2 + vy_smoothing**2)
+    xvec = rotation * np.stack([vx - 1.0, 2.0 / (vx**2 + ay + 1.0), np.cos(vx + 0.5 * vy)], axis=-1)
     E = _su2_exp(-xvec) * np.exp(-1j * np.sin(vy**2))[..., None, None]
     Wm = E @ U0 @ D @ np.conj(U0.T) @ np.conj(np.swapaxes(E, -1, -2))
     return np.ascontiguousarray(np.moveaxis(matrix_to_pauli(Wm), -1, 0))
