@@ -39,9 +39,9 @@ def pool():
 def test_homogeneous_relaxation(qbe, pool):
     """Sec. 5.2 (N = 32, L = 12, J = M = 32, R = 7.5, eq. W0homogeneous, dt = 0.001).  Spin density is
     conserved to round-off (Fig. 2a).  Momentum and energy drift at the rate of the operator's
-    discretisation error for this state (its X(v) has a kink at v_y = 0): 2.8 % and 0.28 % per unit time
-    at N = 32, 18x and 70x less at N = 48 (the oracle alike), far above the 1e-4 / 1e-5 scales of
-    Fig. 2b-c; the library must reproduce the oracle's drift.  Entropy increases every step and the
+    discretisation error for this state (at N = 32 that of its Fermi-Dirac envelope): 2.7 % and 0.28 %
+    per unit time, 58x and 73x less at N = 48 (the oracle alike; at these rates Fig. 2b-c's 1e-4 / 1e-5
+    scales are reached after 4 to 40 steps); the library must reproduce the oracle's drift.  Entropy increases every step and the
     L1 distance to the Fermi-Dirac state of the conserved moments falls (Fig. 4)."""
     N, dt = 32, 0.001
     p = O.Params(N=N, J=32, M=32)
