@@ -623,6 +623,12 @@ def run_collide_only(args, wl, local):
     W = inputs.synthetic_w(N, wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])[:cells]
     w = torch.from_numpy(W.copy()).cuda()
     c = torch.empty_like(w)
+    tuned_ms = None
+    if args.autotune:
+        s.set_state(W.copy())
+        tuned_ms = s.autotune()
+    if args.i3_variant >= 0:
+        s.set_i3_shape(variant=args.i3_variant)
     for _ in range(args.warmup):
         s.collide(w, c)
     torch.cuda.synchronize()
@@ -640,7 +646,8 @@ def run_collide_only(args, wl, local):
             "unit": "cell·k-pts/s", "cells": cells, "steps": args.steps, "warmup": args.warmup,
             "ms_per_eval": t_ms / args.steps, "i3_ms_per_launch": i3_ms / max(i3_n, 1),
             "i3_tflops": flops / (i3_ms / max(i3_n, 1) * 1e-3) / 1e12,
-            "dtype": "f64" if wl.get("precision", 0) == 0 else "f32-split", "workload": wl["name"]}
+            "dtype": "f64" if wl.get("precision", 0) == 0 else "f32-split", "workload": wl["name"],
+            "i3_shape": s.i3_shape(), "autotune_predicted_ms": tuned_ms}
     print(json.dumps(line), flush=True)
     s.close()
     return 0
@@ -893,6 +900,9 @@ def main():
                     help="adjoint_n64: split steps per gradient (default: one checkpoint segment, 20)")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None)
     ap.add_argument("--cells", type=int, default=0)
+    ap.add_argument("--i3-variant", type=int, default=-1,
+                    help="--mode collide: I3 launch variant (qbe_set_i3_shape); default: the library's")
+    ap.add_argument("--autotune", action="store_true", help="--mode collide: run qbe_autotune first")
     ap.add_argument("--cotangents", type=int, default=1,
                     help="--mode vjp: products per call at the same state (shared transforms, up to 4 per group)")
     args = ap.parse_args()

@@ -292,6 +292,35 @@ long long qbe_launch_count(const qbe_handle* h);
 int qbe_enable_timing(qbe_handle* h, int enable);
 int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launches);
 
+/* Launch shape of the I3 (Hu-Ying term, eq. approxH-JM) kernel -- the dominant
+ * part of C[W] (Sec. 3.2) -- and its autotuner.  A shape is
+ *   - a launch variant: one of the kernel forms instantiated for this padded
+ *     grid size 2N and precision.  FP64: the staged kernel with 256 threads and
+ *     64 KB shared-memory chunks (3 blocks per SM) or 128 threads and 32 KB
+ *     chunks (6 per SM).  FP32-split form, 2N = 64, 96, 128: the fused
+ *     shared-memory kernel in two thread/accumulation shapes, or the kernel
+ *     whose element passes go through shared memory; 2N <= 32: the latter
+ *     only; 2N = 192, 256: the cluster kernel only;
+ *   - the persistent grid (blocks; at most the variant's residency);
+ *   - the number of m-chunks per (cell, angle) work unit.
+ * qbe_i3_shape reports the current shape and the number of variants
+ * (any pointer may be NULL).  qbe_i3_variant_name describes a variant (NULL
+ * when out of range; static storage).  qbe_set_i3_shape sets a shape: variant
+ * -1 keeps the variant, grid 0 and m_chunks 0 keep theirs; m_chunks may not
+ * exceed the value set when the handle was created (QBE_ERR_ARG).
+ * qbe_autotune times every variant x grid x m-chunking candidate on the
+ * current state -- two waves of the I3 work queue each, after the per-cell
+ * terms of that state, extrapolated by the number of waves -- and keeps the
+ * fastest; best_ms (may be NULL) receives its predicted I3 launch time.  It
+ * needs a state (QBE_ERR_STATE), synchronises the stream, and leaves the state
+ * unchanged.  The variants compute the same sums in different orders:
+ * results of different shapes agree to rounding (FP64: ~1e-15 relative; the
+ * FP32-split form: within its stated tolerance). */
+int qbe_i3_shape(const qbe_handle* h, int* variant, int* nvariants, int* grid, int* m_chunks);
+const char* qbe_i3_variant_name(const qbe_handle* h, int variant);
+int qbe_set_i3_shape(qbe_handle* h, int variant, int grid, int m_chunks);
+int qbe_autotune(qbe_handle* h, double* best_ms);
+
 /* ------------------------------------------------------------------------
  * Batches of independent simulations: several solver handles -- any mix of
  * N, Nx, J, M, precision, boundary conditions and B fields, all on one
@@ -303,11 +332,12 @@ int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launc
  * padded-grid size and precision whose work queue covers the (simulation,
  * cell, angle, m-chunk) units of every simulation of that size.  Results
  * equal those of qbe_step on each handle (the same kernels on the same units).
- * qbe_batch_autotune times, per simulation, the number of m-chunks per (cell,
- * angle) unit and the I3 grid of single-simulation evaluations on the
- * simulation's current state and keeps the fastest (it drops any captured
- * graph); a changed m-chunking regroups the I3 partial sums (results then
- * differ from untuned steps by rounding).
+ * qbe_batch_autotune chooses, per padded-grid size and precision, the I3
+ * launch shape (variant, persistent grid, m-chunks; see qbe_autotune) of the
+ * group's shared work-queue launch by timing two waves of it per candidate on
+ * the simulations' current states, sets it on every member (qbe_i3_shape
+ * reports it) and drops any captured graph; another shape sums the I3 terms
+ * in another order (results then differ from untuned steps by rounding).
  * The handles stay owned by the caller and must outlive the batch; each may
  * appear once.  With a stream set (qbe_batch_set_stream) the steps are
  * asynchronous on it; without one, qbe_batch_step synchronises before it
@@ -320,7 +350,8 @@ const char* qbe_batch_last_error(const qbe_batch* b);
 int qbe_batch_set_stream(qbe_batch* b, void* stream);
 int qbe_batch_autotune(qbe_batch* b);
 /* Tuned I3 launch shape of simulation `sim` (persistent grid, m-chunks) and
- * the time of one collision evaluation with it (ms, 0 before autotuning). */
+ * the predicted time of its group's I3 launch with it (ms, 0 before
+ * autotuning); the variant is reported by qbe_i3_shape on the handle. */
 int qbe_batch_tuned_shape(const qbe_batch* b, int sim, int* i3_grid, int* m_chunks, double* ms);
 int qbe_batch_step(qbe_batch* b, double dt, int nsteps);
 

@@ -31,39 +31,65 @@ cudaError_t collide_batch(const Tables& t, CollisionWork& cw, const double* w, d
 }
 
 
+#define QBE_SIZE_SWITCH(CALL, FAIL)                                   \
+  if (prec == 1) {                                                    \
+    switch (n) {                                                      \
+      case 16: return CALL(16, float); case 32: return CALL(32, float); \
+      case 64: return CALL(64, float); case 128: return CALL(128, float); \
+      case 256: return CALL(256, float); case 96: return CALL(96, float); \
+      case 192: return CALL(192, float); default: return FAIL;          \
+    }                                                                 \
+  }                                                                   \
+  switch (n) {                                                        \
+    case 16: return CALL(16, double); case 32: return CALL(32, double); \
+    case 64: return CALL(64, double); case 128: return CALL(128, double); \
+    case 256: return CALL(256, double); case 96: return CALL(96, double); \
+    case 192: return CALL(192, double); default: return FAIL;           \
+  }
+
+int i3_variants(int n, int prec) {
+#define QBE_CALL(nn, T) i3_variant_count<nn, T>()
+  QBE_SIZE_SWITCH(QBE_CALL, 0)
+#undef QBE_CALL
+}
+
+int i3_default(int n, int prec) {
+#define QBE_CALL(nn, T) i3_default_variant<nn, T>()
+  QBE_SIZE_SWITCH(QBE_CALL, 0)
+#undef QBE_CALL
+}
+
+int i3_variant_bps(int n, int prec, int variant) {
+#define QBE_CALL(nn, T) i3_blocks_per_sm<nn, T>(variant)
+  QBE_SIZE_SWITCH(QBE_CALL, 1)
+#undef QBE_CALL
+}
+
+const char* i3_variant_desc(int n, int prec, int variant) {
+#define QBE_CALL(nn, T) i3_variant_name<nn, T>(variant)
+  QBE_SIZE_SWITCH(QBE_CALL, nullptr)
+#undef QBE_CALL
+}
+
 cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int prec) {
   const size_t P = (size_t)t.n * t.n;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int bps = 1;
-  if (prec == 1) {
-    switch (t.n) {
-      case 16: bps = i3_blocks_per_sm<16, float>(); break;
-      case 32: bps = i3_blocks_per_sm<32, float>(); break;
-      case 64: bps = i3_blocks_per_sm<64, float>(); break;
-      case 128: bps = i3_blocks_per_sm<128, float>(); break;
-      case 256: bps = i3_blocks_per_sm<256, float>(); break;
-      case 96: bps = i3_blocks_per_sm<96, float>(); break;
-      case 192: bps = i3_blocks_per_sm<192, float>(); break;
-      default: return cudaErrorInvalidValue;
-    }
-  } else {
-    switch (t.n) {
-      case 16: bps = i3_blocks_per_sm<16, double>(); break;
-      case 32: bps = i3_blocks_per_sm<32, double>(); break;
-      case 64: bps = i3_blocks_per_sm<64, double>(); break;
-      case 128: bps = i3_blocks_per_sm<128, double>(); break;
-      case 256: bps = i3_blocks_per_sm<256, double>(); break;
-      case 96: bps = i3_blocks_per_sm<96, double>(); break;
-      case 192: bps = i3_blocks_per_sm<192, double>(); break;
-      default: return cudaErrorInvalidValue;
-    }
+  const int nv = i3_variants(t.n, prec);
+  if (nv < 1) return cudaErrorInvalidValue;
+  const int v0 = i3_default(t.n, prec);
+  const int bps = i3_variant_bps(t.n, prec, v0);
+  int bps_max = bps;
+  for (int v = 0; v < nv; ++v) {
+    const int b = i3_variant_bps(t.n, prec, v);
+    if (b > bps_max) bps_max = b;
   }
   cw.prec = prec;
   cw.nb = nb;
+  cw.i3_variant = v0;
   cw.grid_i3 = nsm * bps;
-  cw.grid_max = cw.grid_i3;
+  cw.grid_max = nsm * bps_max;
   // enough (cell, j, m-chunk) units for about 8 waves of the persistent grid
   int nmc = (8 * cw.grid_i3 + nb * t.J - 1) / (nb * t.J);
   if (nmc < 1) nmc = 1;
@@ -71,9 +97,10 @@ cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int
   cw.mch = (t.M + nmc - 1) / nmc;
   cw.nmc = (t.M + cw.mch - 1) / cw.mch;
   const size_t nparts = (size_t)nb * t.J * cw.nmc;
+  cw.nparts_cap = nparts;
   cw.ws_slots = nb > cw.grid_i3 ? nb : cw.grid_i3;
   size_t ws_fields = 6 * (size_t)nb;
-  if (3 * (size_t)cw.grid_i3 > ws_fields) ws_fields = 3 * (size_t)cw.grid_i3;
+  if (3 * (size_t)cw.grid_max > ws_fields) ws_fields = 3 * (size_t)cw.grid_max;
   cw.ws_fields = ws_fields;
   const size_t N = t.N;
   const size_t cz = prec == 1 ? sizeof(float2) : sizeof(double2);   // complex element
@@ -151,12 +178,12 @@ cudaError_t collide_post(const Tables& t, CollisionWork& cw, double* c, int ncel
 }
 
 cudaError_t i3_group(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
-                     void* ws, int grid, cudaStream_t s, long long& launches) {
+                     void* ws, int grid, cudaStream_t s, long long& launches, int max_units) {
   if (njobs < 1) return cudaErrorInvalidValue;
   const Tables& t = *tabs[0];
   for (int k = 1; k < njobs; ++k)
     if (tabs[k]->n != t.n || cws[k]->prec != cws[0]->prec) return cudaErrorInvalidValue;
-#define QBE_GROUP_CALL(n, T) i3_group_n<n, T>(tabs, cws, ncells, njobs, ws, grid, s, launches)
+#define QBE_GROUP_CALL(n, T) i3_group_n<n, T>(tabs, cws, ncells, njobs, ws, grid, s, launches, max_units)
   if (cws[0]->prec == 1) {
     QBE_VJP_SWITCH(float, QBE_GROUP_CALL)
   } else {

@@ -248,23 +248,11 @@ __global__ void __launch_bounds__(kThreads) k_i24(const typename Vec2Of<T>::type
 // The unit's partial sum acc[2][n*n] (pairs (0,1), (2,3), real space) is
 // written to its own slot of K3part and reduced in fixed order later.
 // --------------------------------------------------------------------------
-// Launch shape of the staged I3 kernel (FP64 on every grid; the FP32-split form uses k_i3_smem up
-// to 128 points and k_i3_cluster above): three 256-thread blocks per SM with 64 KB chunks.
-template <int n, class T>
-__host__ __device__ constexpr int i3_threads() {
-  return kThreads;
-}
-template <int n, class T>
-__host__ __device__ constexpr int i3_min_blocks() {
-  return 3;
-}
-template <int n, class T>
-__host__ __device__ constexpr int i3_chunk_bytes() {
-  return 65536;
-}
-
-template <int n, class T>
-__global__ void __launch_bounds__(i3_threads<n, T>(), i3_min_blocks<n, T>())
+// The staged kernel's launch shape (threads per block, shared-memory chunk bytes of its row and
+// column passes, blocks per SM) is a template parameter: the autotuner chooses among the
+// instantiated shapes (i3_variant below).
+template <int n, class T, int NTH = 256, int CB = 65536, int MINB = 3>
+__global__ void __launch_bounds__(NTH, MINB)
     k_i3(const I3Jobs<T> jobs, typename Vec2Of<T>::type* ws, const typename Vec2Of<T>::type* __restrict__ gtw) {
   using C2 = typename Vec2Of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -308,11 +296,11 @@ __global__ void __launch_bounds__(i3_threads<n, T>(), i3_min_blocks<n, T>())
         const C2* in = what + ((size_t)c * 4 + p) * P;
         C2* S = Sig + (size_t)p * P;
         // only the n/2 columns (y frequencies) of Xi are non-zero: transform those
-        col_pass_list<n, 1, false, 0, i3_chunk_bytes<n, T>()>(
+        col_pass_list<n, 1, false, 0, CB>(
             sm, tw, xcols, n / 2,
             [&](int ix, int iy) { return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<T>(); },
             NoMid(), [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
-        row_pass<n, 1, false, 0, i3_chunk_bytes<n, T>()>(
+        row_pass<n, 1, false, 0, CB>(
             sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : zero2<T>(); }, NoMid(),
             [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
       }
@@ -324,18 +312,18 @@ __global__ void __launch_bounds__(i3_threads<n, T>(), i3_min_blocks<n, T>())
         for (int p = 0; p < 2; ++p) {
           const C2* Sp = Sig + (size_t)p * P;
           C2* accp = acc + (size_t)p * P;
-          row_pass<n, -1, false, 0, i3_chunk_bytes<n, T>()>(
+          row_pass<n, -1, false, 0, CB>(
               sm, tw,
               [&](int ix, int iy) {
                 const C2 z = wa[ix * n + iy];
                 return cscale(Sp[ix * n + iy], im ? z.y : z.x);
               },
               NoMid(), [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
-          col_conv_pass<n, i3_chunk_bytes<n, T>()>(
+          col_conv_pass<n, CB>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; },
               [&](int ix, int iy) { return psp[ix * n + iy]; },
               [&](int ix, int iy, C2 v) { G[ix * n + iy] = v; });
-          row_pass<n, 1, false, 0, i3_chunk_bytes<n, T>()>(
+          row_pass<n, 1, false, 0, CB>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
               [&](int ix, int iy, C2 v) {
                 const C2 s = Sa[ix * n + iy];
@@ -463,6 +451,28 @@ template <int n>
 constexpr size_t i3_smem_bytes() {   // twiddles, the field (padded rows), psi'_j
   return (size_t)(n + n * (n + 1)) * sizeof(float2) + (size_t)n * n * sizeof(float);
 }
+
+#include "i3_fused.cuh"
+
+// Padded sizes with the fused shared-memory FP32 kernel (whole row tasks per thread for its shapes).
+template <int n>
+__host__ __device__ constexpr bool use_i3_fused() {
+  return n == 64 || n == 96 || n == 128;
+}
+// Its launch shapes per size: (threads, blocks per SM, accumulation mode of k_i3_fused), and the
+// default variant (I3 launch of 128 cells, J = M = 32, on a GB300: N = 32 28.6 ms for shape 0,
+// 32.5 and 35.4 for shapes 1 and 2, 31.0 for k_i3_smem; N = 48 74.7 ms for k_i3_smem, 77.5, 81.7,
+// 108.6 for the fused shapes; N = 64 100.9 ms for shape 0, 116.3, 112.1, 124.0 for k_i3_smem).
+template <int n> struct FusedShapes;
+template <> struct FusedShapes<64> {
+  static constexpr int T0 = 512, B0 = 2, M0 = 1, T1 = 512, B1 = 2, M1 = 2, T2 = 256, B2 = 4, M2 = 2, DEFAULT = 0;
+};
+template <> struct FusedShapes<96> {
+  static constexpr int T0 = 768, B0 = 1, M0 = 0, T1 = 768, B1 = 1, M1 = 2, T2 = 384, B2 = 2, M2 = 2, DEFAULT = 3;
+};
+template <> struct FusedShapes<128> {
+  static constexpr int T0 = 512, B0 = 1, M0 = 1, T1 = 1024, B1 = 1, M1 = 2, T2 = 1024, B2 = 1, M2 = 0, DEFAULT = 0;
+};
 
 // --------------------------------------------------------------------------
 // I3 on padded grids above 128 points in FP32 (n = 192, 256: one field is 288 or 512 KB, more
@@ -743,10 +753,67 @@ size_t smem_bytes() {
   return (size_t)(n + Chunk<n, sizeof(C2)>::SMEM_ELEMS) * sizeof(C2);
 }
 
-template <int n, class T>
+template <int n, class T, int CB>
 size_t i3_staged_smem_bytes() {
   using C2 = typename Vec2Of<T>::type;
-  return (size_t)(n + Chunk<n, sizeof(C2), i3_chunk_bytes<n, T>()>::SMEM_ELEMS) * sizeof(C2);
+  return (size_t)(n + Chunk<n, sizeof(C2), CB>::SMEM_ELEMS) * sizeof(C2);
+}
+
+// Launch variants of the I3 kernel for padded size n and transform type T: the shapes the
+// autotuner chooses among (i3_default_variant gives the one a new handle starts with).
+//   FP64 (every size): the staged kernel as (threads, chunk bytes, blocks per SM)
+//     0: (256, 64 KB, 3)   1: (128, 32 KB, 6)
+//   FP32, n = 64, 96, 128: 0, 1, 2: the fused shared-memory kernel in the FusedShapes<n> shapes,
+//     3: k_i3_smem (1024 threads, element passes through shared memory)
+//   FP32, n <= 32: k_i3_smem;  FP32, n > 128: the cluster kernel.
+struct I3Launch {
+  const void* fn = nullptr;
+  int threads = 0;
+  size_t smem = 0;
+  bool cluster = false;
+  const char* name = "";
+};
+
+template <int n, class T>
+constexpr int i3_nvariants() {
+  if constexpr (std::is_same<T, float>::value) {
+    if constexpr (use_i3_cluster<n>()) return 1;
+    else if constexpr (use_i3_fused<n>()) return 4;
+    else return 1;
+  } else {
+    return 2;
+  }
+}
+
+template <int n, class T>
+I3Launch i3_variant(int v) {
+  I3Launch l;
+  if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
+    l = {(const void*)k_i3_cluster<n>, kThreadsI3Cluster, i3_cluster_smem_bytes<n>(), true,
+         "cluster of 4 CTAs x 1024 threads"};
+  } else if constexpr (std::is_same<T, float>::value && use_i3_fused<n>()) {
+    using S = FusedShapes<n>;
+    constexpr const char* names[3] = {"fused, per-convolution partial sums", "fused, register accumulation",
+                                      "fused, paired w with register accumulation"};
+    if (v == 0)
+      l = {(const void*)k_i3_fused<n, S::T0, S::B0, S::M0>, S::T0, i3_fused_smem_bytes<n>(), false, names[S::M0]};
+    else if (v == 1)
+      l = {(const void*)k_i3_fused<n, S::T1, S::B1, S::M1>, S::T1, i3_fused_smem_bytes<n>(), false, names[S::M1]};
+    else if (v == 2)
+      l = {(const void*)k_i3_fused<n, S::T2, S::B2, S::M2>, S::T2, i3_fused_smem_bytes<n>(), false, names[S::M2]};
+    else
+      l = {(const void*)k_i3_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>(), false, "shared-memory, 1024 threads"};
+  } else if constexpr (std::is_same<T, float>::value) {
+    l = {(const void*)k_i3_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>(), false, "shared-memory, 1024 threads"};
+  } else {
+    if (v == 1)
+      l = {(const void*)k_i3<n, T, 128, 32768, 6>, 128, i3_staged_smem_bytes<n, T, 32768>(), false,
+           "staged, 128 threads, 32 KB chunks"};
+    else
+      l = {(const void*)k_i3<n, T, 256, 65536, 3>, 256, i3_staged_smem_bytes<n, T, 65536>(), false,
+           "staged, 256 threads, 64 KB chunks"};
+  }
+  return l;
 }
 
 template <int n, class T>
@@ -758,13 +825,10 @@ void set_smem_attributes() {
   cudaFuncSetAttribute(k_i1<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_i24<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_assemble<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
-    cudaFuncSetAttribute(k_i3_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
-  else if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>())
-    cudaFuncSetAttribute(k_i3_cluster<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)i3_cluster_smem_bytes<n>());
-  else
-    cudaFuncSetAttribute(k_i3<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_staged_smem_bytes<n, T>());
+  for (int v = 0; v < i3_nvariants<n, T>(); ++v) {
+    const I3Launch l = i3_variant<n, T>(v);
+    cudaFuncSetAttribute(l.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem);
+  }
 }
 
 // Clusters of k_i3_cluster<n> that can be resident at once on the current device (cached per device).
@@ -788,18 +852,41 @@ int i3_max_clusters() {
   return cached[dev & 63];
 }
 
+// Resident blocks per SM of an I3 variant (at least 1).
 template <int n, class T>
-int i3_blocks_per_sm() {
+int i3_blocks_per_sm(int v) {
   set_smem_attributes<n, T>();
+  if (v < 0 || v >= i3_nvariants<n, T>()) v = 0;
+  const I3Launch l = i3_variant<n, T>(v);
   int b = 0;
-  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>());
-  else if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>())
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_cluster<n>, kThreadsI3Cluster,
-                                                  i3_cluster_smem_bytes<n>());
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3<n, T>, i3_threads<n, T>(), i3_staged_smem_bytes<n, T>());
+  if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    b = (i3_max_clusters<n>() * kI3Cluster + nsm - 1) / (nsm > 0 ? nsm : 1);
+  } else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, l.fn, l.threads, l.smem) != cudaSuccess) {
+    cudaGetLastError();
+    b = 1;
+  }
   return b < 1 ? 1 : b;
+}
+
+template <int n, class T>
+int i3_variant_count() {
+  return i3_nvariants<n, T>();
+}
+
+// The variant a new handle starts with (the fastest measured on a GB300 for this size).
+template <int n, class T>
+int i3_default_variant() {
+  if constexpr (std::is_same<T, float>::value && use_i3_fused<n>()) return FusedShapes<n>::DEFAULT;
+  else return 0;
+}
+
+template <int n, class T>
+const char* i3_variant_name(int v) {
+  if (v < 0 || v >= i3_nvariants<n, T>()) return nullptr;
+  return i3_variant<n, T>(v).name;
 }
 
 // The collision operator in three parts: the per-cell terms before I3 (prep, I1, I2/I4), the I3
@@ -854,7 +941,7 @@ I3Job<T> i3_job(const Tables& t, const CollisionWork& cw, int ncells, int unit_b
 // of kI3Cluster blocks).
 template <int n, class T>
 cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
-                       void* ws, int grid, cudaStream_t s, long long& launches) {
+                       void* ws, int grid, cudaStream_t s, long long& launches, int max_units) {
   using C2 = typename Vec2Of<T>::type;
   if (njobs < 1 || njobs > kMaxI3Jobs) return cudaErrorInvalidValue;
   set_smem_attributes<n, T>();
@@ -865,24 +952,34 @@ cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cw
     jobs.job[k] = i3_job<n, T>(*tabs[k], *cws[k], ncells[k], total);
     total += jobs.job[k].nunits;
   }
-  jobs.total = total;
+  jobs.total = (max_units > 0 && max_units < total) ? max_units : total;   // a prefix (autotuner samples)
+  total = jobs.total;
   if (total == 0) return cudaSuccess;
-  const int g = total < grid ? total : grid;
   const TabPtrs<T> tb = tab_ptrs<T>(*tabs[0]);
-  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>()) {
-    k_i3_smem<n><<<g, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(jobs, (C2*)ws, tb.tw);
-  } else if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
+  int v = cws[0]->i3_variant;
+  if (v < 0 || v >= i3_nvariants<n, T>()) v = 0;
+  const I3Launch l = i3_variant<n, T>(v);
+  int g = total < grid ? total : grid;
+  if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
     int ncl = grid / kI3Cluster;
     const int cmax = i3_max_clusters<n>();
     if (ncl > cmax) ncl = cmax;
     if (ncl > total) ncl = total;
     if (ncl < 1) ncl = 1;
-    k_i3_cluster<n><<<ncl * kI3Cluster, kThreadsI3Cluster, i3_cluster_smem_bytes<n>(), s>>>(jobs, (C2*)ws, tb.tw);
+    g = ncl * kI3Cluster;
   } else {
-    k_i3<n, T><<<g, i3_threads<n, T>(), i3_staged_smem_bytes<n, T>(), s>>>(jobs, (C2*)ws, tb.tw);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int gmax = nsm * i3_blocks_per_sm<n, T>(v);      // persistent: never more than fit at once
+    if (g > gmax) g = gmax;
   }
+  C2* wsp = (C2*)ws;
+  const C2* twp = tb.tw;
+  void* args[] = {(void*)&jobs, (void*)&wsp, (void*)&twp};
+  cudaError_t e = cudaLaunchKernel(l.fn, dim3(g), dim3(l.threads), args, l.smem, s);
   ++launches;
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int n, class T>
@@ -908,7 +1005,7 @@ cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w,
   const Tables* tp = &t;
   const CollisionWork* cp = &cw;
   if (tm) tm->begin(KG_I3, s);
-  e = i3_group_n<n, T>(&tp, &cp, &ncells, 1, cw.ws, cw.grid_i3, s, launches);
+  e = i3_group_n<n, T>(&tp, &cp, &ncells, 1, cw.ws, cw.grid_i3, s, launches, 0);
   if (tm) tm->end(s);
   if (e != cudaSuccess) return e;
   return collide_post_n<n, T>(t, cw, c, ncells, s, launches, tm);

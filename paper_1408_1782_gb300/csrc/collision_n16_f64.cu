@@ -4,7 +4,10 @@
 namespace qbe {
 template cudaError_t collide_batch_n<16, double>(const Tables&, CollisionWork&, const double*, double*, int,
                                               cudaStream_t, long long&, KernelTimer*);
-template int i3_blocks_per_sm<16, double>();
+template int i3_blocks_per_sm<16, double>(int);
+template int i3_variant_count<16, double>();
+template int i3_default_variant<16, double>();
+template const char* i3_variant_name<16, double>(int);
 template cudaError_t collide_vjp_n<16, double>(const Tables&, CollisionWork&, VjpWork&, const double*,
                                               const double* const*, double* const*, int, int, int, cudaStream_t,
                                               long long&, KernelTimer*);
@@ -14,5 +17,5 @@ template cudaError_t collide_pre_n<16, double>(const Tables&, CollisionWork&, co
 template cudaError_t collide_post_n<16, double>(const Tables&, CollisionWork&, double*, int, cudaStream_t, long long&,
                                              KernelTimer*);
 template cudaError_t i3_group_n<16, double>(const Tables* const*, const CollisionWork* const*, const int*, int, void*,
-                                         int, cudaStream_t, long long&);
+                                         int, cudaStream_t, long long&, int);
 }  // namespace qbe

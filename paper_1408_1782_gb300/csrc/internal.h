@@ -78,7 +78,9 @@ struct CollisionWork {
   int nmc = 1;         // m-chunks per (cell, j) unit of the I3 kernel
   int mch = 1;         // m values per chunk
   int grid_i3 = 0;     // persistent grid of the I3 kernel
-  int grid_max = 0;    // its occupancy limit (SMs x resident blocks)
+  int grid_max = 0;    // its occupancy limit (SMs x resident blocks, the largest over the variants)
+  int i3_variant = 0;  // launch variant of the I3 kernel (i3_variants)
+  size_t nparts_cap = 0;  // (cell, j, m-chunk) units the partial-sum buffer K3part holds
   // buffers of the transform precision (complex = double2 or float2)
   void* what = nullptr;      // [nb][4][n*n] spectral pairs (w0+iw1, w2+iw3, w1+iw2, w3)
   void* wfine = nullptr;     // [nb][2][n*n] fine-grid fields (w0+iw1, w2+iw3)
@@ -197,7 +199,19 @@ template <int n, class T>
 cudaError_t collide_batch_n(const Tables& t, CollisionWork& cw, const double* w, double* c, int ncells, cudaStream_t s,
                             long long& launches, KernelTimer* tm);
 template <int n, class T>
-int i3_blocks_per_sm();
+int i3_blocks_per_sm(int variant);
+template <int n, class T>
+int i3_variant_count();
+template <int n, class T>
+int i3_default_variant();
+template <int n, class T>
+const char* i3_variant_name(int variant);
+// Launch variants of the I3 kernel ("tile shapes" the autotuner chooses among) for a grid and
+// precision: their number, resident blocks per SM, and a description.
+int i3_variants(int n, int prec);
+int i3_default(int n, int prec);
+int i3_variant_bps(int n, int prec, int variant);
+const char* i3_variant_desc(int n, int prec, int variant);
 // The collision operator in parts (collision_kernels.cuh): the per-cell terms before I3, the I3
 // work queue over one or several simulations of the same padded size, the per-cell assembly.
 cudaError_t collide_pre(const Tables& t, CollisionWork& cw, const double* w, int ncells, cudaStream_t s,
@@ -205,7 +219,7 @@ cudaError_t collide_pre(const Tables& t, CollisionWork& cw, const double* w, int
 cudaError_t collide_post(const Tables& t, CollisionWork& cw, double* c, int ncells, cudaStream_t s,
                          long long& launches);
 cudaError_t i3_group(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
-                     void* ws, int grid, cudaStream_t s, long long& launches);
+                     void* ws, int grid, cudaStream_t s, long long& launches, int max_units = 0);
 template <int n, class T>
 cudaError_t collide_pre_n(const Tables& t, CollisionWork& cw, const double* w, int ncells, cudaStream_t s,
                           long long& launches, KernelTimer* tm);
@@ -214,7 +228,7 @@ cudaError_t collide_post_n(const Tables& t, CollisionWork& cw, double* c, int nc
                            long long& launches, KernelTimer* tm);
 template <int n, class T>
 cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cws, const int* ncells, int njobs,
-                       void* ws, int grid, cudaStream_t s, long long& launches);
+                       void* ws, int grid, cudaStream_t s, long long& launches, int max_units);
 void free_collision_work(CollisionWork& cw);
 
 // Vector-Jacobian products of the collision operator (collision_vjp.cuh) at

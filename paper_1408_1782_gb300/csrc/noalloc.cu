@@ -240,7 +240,7 @@ extern "C" int qbe_collide_noalloc(const qbe_grid* g, const double* w, double* c
   t.psip_s = (double*)(base + lay.psip);
   t.phase = (double2*)(base + lay.phase);
   qbe::CollisionWork cw;
-  cw.nb = nb; cw.nmc = 1; cw.mch = g->M; cw.grid_i3 = grid;
+  cw.nb = nb; cw.nmc = 1; cw.mch = g->M; cw.grid_i3 = grid; cw.nparts_cap = (size_t)nb * g->J;
   unsigned char* wp = base + lay.tables_end;
   auto take = [&](size_t bytes) { unsigned char* r = wp; wp += align256(bytes); return r; };
   cw.what = (double2*)take((size_t)nb * 4 * P * sizeof(double2));

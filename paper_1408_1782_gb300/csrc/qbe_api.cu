@@ -71,6 +71,8 @@ struct qbe_handle {
 
 namespace {
 
+int tune_group(const std::vector<qbe_handle*>& hs, cudaStream_t s, double* best_ms, std::string& err);
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -349,6 +351,47 @@ int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launc
   if (total_ms) *total_ms = h->timer.total_ms[which];
   if (launches) *launches = h->timer.count[which];
   return QBE_OK;
+}
+
+int qbe_i3_shape(const qbe_handle* h, int* variant, int* nvariants, int* grid, int* m_chunks) {
+  if (!h) return QBE_ERR_ARG;
+  if (variant) *variant = h->cw.i3_variant;
+  if (nvariants) *nvariants = i3_variants(h->tab.n, h->cw.prec);
+  if (grid) *grid = h->cw.grid_i3;
+  if (m_chunks) *m_chunks = h->cw.nmc;
+  return QBE_OK;
+}
+
+const char* qbe_i3_variant_name(const qbe_handle* h, int variant) {
+  if (!h) return nullptr;
+  return i3_variant_desc(h->tab.n, h->cw.prec, variant);
+}
+
+int qbe_set_i3_shape(qbe_handle* h, int variant, int grid, int m_chunks) {
+  if (!h) return QBE_ERR_ARG;
+  if (variant < -1 || variant >= i3_variants(h->tab.n, h->cw.prec) || grid < 0 || m_chunks < 0)
+    return fail(h, QBE_ERR_ARG, "set_i3_shape: variant, grid or m-chunks out of range");
+  const int cap_nmc = (int)(h->cw.nparts_cap / ((size_t)h->cw.nb * h->tab.J));
+  if (m_chunks > cap_nmc) return fail(h, QBE_ERR_ARG, "set_i3_shape: more m-chunks than the partial sums hold");
+  if (variant >= 0) h->cw.i3_variant = variant;
+  if (grid > 0) {
+    const int cap = (int)(h->cw.ws_fields / 3);
+    h->cw.grid_i3 = grid < cap ? grid : cap;
+  }
+  if (m_chunks > 0) {
+    h->cw.mch = (h->tab.M + m_chunks - 1) / m_chunks;
+    h->cw.nmc = (h->tab.M + h->cw.mch - 1) / h->cw.mch;
+  }
+  return QBE_OK;
+}
+
+int qbe_autotune(qbe_handle* h, double* best_ms) {
+  if (!h) return QBE_ERR_ARG;
+  if (!h->has_state) return fail(h, QBE_ERR_STATE, "autotune: no state");
+  DeviceGuard dg(h->g.device);
+  std::string err;
+  const int rc = tune_group({h}, h->stream, best_ms, err);
+  return rc == QBE_OK ? rc : fail(h, rc, err);
 }
 
 int qbe_set_stream(qbe_handle* h, void* stream) {
@@ -803,6 +846,103 @@ struct qbe_batch {
 
 namespace {
 
+// The I3 launch shape of a group of simulations of one padded size and precision (a single
+// simulation is a group of one): for every launch variant, persistent grid (blocks per SM) and
+// m-chunking, two waves of the group's work queue are timed on the simulations' current state
+// (the per-cell terms are computed first, so the I3 inputs are those of the state) and the launch
+// time is extrapolated by waves, ceil(units / grid) x (time per wave).  The fastest shape is set
+// on every member; returns its predicted launch time in ms.
+int tune_group(const std::vector<qbe_handle*>& hs, cudaStream_t s, double* best_ms, std::string& err) {
+  if (hs.empty()) return QBE_ERR_ARG;
+  qbe_handle* h0 = hs[0];
+  const int n = h0->tab.n, prec = h0->cw.prec;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->g.device);
+  std::vector<int> nc(hs.size()), nmc_max(hs.size());
+  std::vector<const Tables*> tabs;
+  std::vector<const CollisionWork*> cws;
+  long long scratch = 0;
+  for (size_t i = 0; i < hs.size(); ++i) {
+    qbe_handle* h = hs[i];
+    if (!h->has_state) { err = "autotune: a simulation has no state"; return QBE_ERR_STATE; }
+    nc[i] = h->g.Nx < h->cw.nb ? h->g.Nx : h->cw.nb;
+    if (collide_pre(h->tab, h->cw, h->W, nc[i], s, scratch) != cudaSuccess) {
+      err = "autotune: per-cell terms failed";
+      return QBE_ERR_CUDA;
+    }
+    // the largest m-chunking the partial-sum buffers hold (set at allocation, or by an earlier tuning)
+    nmc_max[i] = (int)(h->cw.nparts_cap / ((size_t)h->cw.nb * h->tab.J));
+    if (nmc_max[i] < 1) nmc_max[i] = 1;
+    tabs.push_back(&h->tab);
+    cws.push_back(&h->cw);
+  }
+  int nmc_top = 1;
+  for (int v : nmc_max) nmc_top = v > nmc_top ? v : nmc_top;
+  const int ws_blocks = (int)(h0->cw.ws_fields / 3);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    err = "autotune: event creation failed";
+    return QBE_ERR_CUDA;
+  }
+  auto apply = [&](int v, int nmc) {
+    for (size_t i = 0; i < hs.size(); ++i) {
+      CollisionWork& cw = hs[i]->cw;
+      const int M = hs[i]->tab.M;
+      const int want = nmc < nmc_max[i] ? nmc : nmc_max[i];
+      cw.i3_variant = v;
+      cw.mch = (M + want - 1) / want;
+      cw.nmc = (M + cw.mch - 1) / cw.mch;
+    }
+  };
+  double best = 1e300;
+  int bv = 0, bgrid = h0->cw.grid_i3, bnmc = h0->cw.nmc;
+  int rc = QBE_OK;
+  const int nv = i3_variants(n, prec);
+  for (int v = 0; v < nv && rc == QBE_OK; ++v) {
+    const int bpsv = i3_variant_bps(n, prec, v);
+    for (int bps = 1; bps <= bpsv && rc == QBE_OK; ++bps) {
+      int grid = bps * nsm;
+      if (grid > ws_blocks) grid = ws_blocks;
+      if (grid < 1) grid = 1;
+      for (int nmc = nmc_top; nmc >= 1 && rc == QBE_OK; nmc = (nmc == 1 ? 0 : (nmc + 1) / 2)) {
+        apply(v, nmc);
+        long long total = 0;
+        for (size_t i = 0; i < hs.size(); ++i) total += (long long)nc[i] * hs[i]->tab.J * hs[i]->cw.nmc;
+        const int sample = (int)(total < 2LL * grid ? total : 2LL * grid);
+        long long lc = 0;
+        cudaError_t e = i3_group(tabs.data(), cws.data(), nc.data(), (int)hs.size(), h0->cw.ws, grid, s, lc, sample);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess)
+          e = i3_group(tabs.data(), cws.data(), nc.data(), (int)hs.size(), h0->cw.ws, grid, s, lc, sample);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          err = std::string("autotune: timing run failed: ") + cudaGetErrorString(e);
+          rc = QBE_ERR_CUDA;
+          break;
+        }
+        // the kernel caps the grid at the variant's residency; waves over the launched blocks
+        int g = grid;
+        const int gres = nsm * i3_variant_bps(n, prec, v);
+        if (g > gres) g = gres;
+        const double per_wave = ms / (double)((sample + g - 1) / g);
+        const double pred = per_wave * (double)((total + g - 1) / g);
+        if (pred < best) { best = pred; bv = v; bgrid = grid; bnmc = nmc; }
+        if (nmc == 1) break;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != QBE_OK) return rc;
+  apply(bv, bnmc);
+  for (auto h : hs) h->cw.grid_i3 = bgrid;
+  if (best_ms) *best_ms = best;
+  return QBE_OK;
+}
+
 int bfail(qbe_batch* b, int code, const std::string& msg) {
   b->err = msg;
   return code;
@@ -820,6 +960,25 @@ void drop_graph(qbe_batch* b) {
 // precision runs a work queue over the (simulation, cell, j, m-chunk) units of all simulations of
 // that size (Sec. 3.2; the simulations are independent).  Per simulation the arithmetic is that of
 // do_step: the same kernels on the same units.
+// Groups of simulations sharing the I3 kernel (padded size and precision), at most kMaxI3Jobs each.
+std::vector<std::vector<size_t>> i3_groups(const qbe_batch* b) {
+  std::vector<std::vector<size_t>> groups;
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    const qbe_handle* h = b->sims[i];
+    bool placed = false;
+    for (auto& g : groups) {
+      const qbe_handle* h0 = b->sims[g[0]];
+      if (h0->tab.n == h->tab.n && h0->cw.prec == h->cw.prec && (int)g.size() < kMaxI3Jobs) {
+        g.push_back(i);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) groups.push_back({i});
+  }
+  return groups;
+}
+
 int batch_capture_step(qbe_batch* b, double dt, cudaStream_t origin) {
   const size_t ns = b->sims.size();
   auto branch = [&](size_t i) { return origin == b->side[i] ? origin : b->side[i]; };
@@ -835,21 +994,7 @@ int batch_capture_step(qbe_batch* b, double dt, cudaStream_t origin) {
         cudaStreamWaitEvent(origin, b->join[i], 0);
       }
   };
-  // groups of simulations sharing the I3 kernel (padded size and precision), at most kMaxI3Jobs each
-  std::vector<std::vector<size_t>> groups;
-  for (size_t i = 0; i < ns; ++i) {
-    const qbe_handle* h = b->sims[i];
-    bool placed = false;
-    for (auto& g : groups) {
-      const qbe_handle* h0 = b->sims[g[0]];
-      if (h0->tab.n == h->tab.n && h0->cw.prec == h->cw.prec && (int)g.size() < kMaxI3Jobs) {
-        g.push_back(i);
-        placed = true;
-        break;
-      }
-    }
-    if (!placed) groups.push_back({i});
-  }
+  const std::vector<std::vector<size_t>> groups = i3_groups(b);
   auto i3_all = [&](long long& launches) {
     for (auto& g : groups) {
       std::vector<const Tables*> tabs;
@@ -861,10 +1006,9 @@ int batch_capture_step(qbe_batch* b, double dt, cudaStream_t origin) {
         nc.push_back(b->sims[i]->g.Nx);
       }
       const CollisionWork& c0 = b->sims[g[0]]->cw;
-      const int grid = (int)(c0.ws_fields / 3);           // blocks the first simulation's scratch can hold
-      const int gmax = c0.grid_max;
-      cudaError_t e = i3_group(tabs.data(), cws.data(), nc.data(), (int)g.size(), c0.ws, grid < gmax ? grid : gmax,
-                               origin, launches);
+      const int cap = (int)(c0.ws_fields / 3);            // blocks the first simulation's scratch can hold
+      const int grid = c0.grid_i3 < cap ? c0.grid_i3 : cap;   // the group's (tuned) persistent grid
+      cudaError_t e = i3_group(tabs.data(), cws.data(), nc.data(), (int)g.size(), c0.ws, grid, origin, launches);
       if (e != cudaSuccess) return QBE_ERR_CUDA;
     }
     return QBE_OK;
@@ -978,51 +1122,18 @@ int qbe_batch_autotune(qbe_batch* b) {
   if (!b) return QBE_ERR_ARG;
   DeviceGuard dg(b->device);
   drop_graph(b);                                       // launch shapes are baked into the graph
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return bfail(b, QBE_ERR_CUDA, "autotune: event creation failed");
-  int rc = QBE_OK;
-  for (size_t i = 0; i < b->sims.size() && rc == QBE_OK; ++i) {
-    qbe_handle* h = b->sims[i];
-    if (!h->has_state) { rc = bfail(b, QBE_ERR_STATE, "autotune: a simulation has no state"); break; }
-    CollisionWork& cw = h->cw;
-    const int grid_max = cw.grid_i3, nmc_max = cw.nmc;
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
-    const bool was_on = h->timer.on;
-    h->timer.on = false;
-    double best = 1e300;
-    int best_grid = grid_max, best_nmc = nmc_max;
-    // candidates: persistent I3 grid of 1..3 blocks per SM, m-chunk counts nmc_max, nmc_max/2, .., 1
-    for (int bps = 1; bps * nsm <= grid_max; ++bps) {
-      for (int nmc = nmc_max; nmc >= 1; nmc = (nmc == 1 ? 0 : (nmc + 1) / 2)) {
-        cw.grid_i3 = bps * nsm;
-        cw.mch = (h->g.M + nmc - 1) / nmc;
-        cw.nmc = (h->g.M + cw.mch - 1) / cw.mch;
-        int r = do_collide_dev(h, h->W, h->Cb, h->g.Nx);                    // warm
-        cudaEventRecord(e0, h->stream);
-        if (!r) r = do_collide_dev(h, h->W, h->Cb, h->g.Nx);
-        cudaEventRecord(e1, h->stream);
-        float ms = 0.f;
-        if (!r && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
-          if (ms < best) { best = ms; best_grid = cw.grid_i3; best_nmc = cw.nmc; }
-        } else {
-          rc = bfail(b, QBE_ERR_CUDA, "autotune: timing run failed");
-          break;
-        }
-        if (nmc == 1) break;
-      }
-      if (rc) break;
-    }
-    cw.grid_i3 = best_grid;
-    cw.mch = (h->g.M + best_nmc - 1) / best_nmc;
-    cw.nmc = (h->g.M + cw.mch - 1) / cw.mch;
-    h->timer.on = was_on;
-    b->tuned_ms[i] = best;
+  cudaStream_t s = b->stream ? b->stream : b->side[0];
+  std::vector<std::vector<size_t>> groups = i3_groups(b);
+  for (auto& g : groups) {
+    std::vector<qbe_handle*> hs;
+    for (size_t i : g) hs.push_back(b->sims[i]);
+    double ms = 0.0;
+    std::string err;
+    const int rc = tune_group(hs, s, &ms, err);
+    if (rc != QBE_OK) return bfail(b, rc, err);
+    for (size_t i : g) b->tuned_ms[i] = ms;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  return rc;
+  return QBE_OK;
 }
 
 int qbe_batch_tuned_shape(const qbe_batch* b, int sim, int* i3_grid, int* m_chunks, double* ms) {

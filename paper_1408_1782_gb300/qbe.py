@@ -87,6 +87,11 @@ SIGNATURES = {
     "qbe_dilog": (_c_double, [_c_double]),
     "qbe_relative_entropy": (_c_int, [_c_void_p, _c_void_p, _c_int, _c_void_p, _c_void_p, _c_int]),
     "qbe_collide_noalloc": (_c_int, [ctypes.POINTER(QbeGrid), _c_void_p, _c_void_p, _c_int, _c_void_p]),
+    "qbe_i3_shape": (_c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                              ctypes.POINTER(_c_int)]),
+    "qbe_i3_variant_name": (ctypes.c_char_p, [_c_void_p, _c_int]),
+    "qbe_set_i3_shape": (_c_int, [_c_void_p, _c_int, _c_int, _c_int]),
+    "qbe_autotune": (_c_int, [_c_void_p, ctypes.POINTER(_c_double)]),
     "qbe_batch_create": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, ctypes.POINTER(_c_void_p)]),
     "qbe_batch_destroy": (None, [_c_void_p]),
     "qbe_batch_last_error": (ctypes.c_char_p, [_c_void_p]),
@@ -458,6 +463,28 @@ class Solver:
         self._check(lib().qbe_kernel_time(self._h, KERNEL_GROUPS[group], ctypes.byref(ms), ctypes.byref(n)),
                     "qbe_kernel_time")
         return ms.value, n.value
+
+    def i3_shape(self):
+        """Current I3 launch shape: dict(variant, nvariants, grid, m_chunks, name)."""
+        v, nv, g, m = _c_int(), _c_int(), _c_int(), _c_int()
+        self._check(lib().qbe_i3_shape(self._h, ctypes.byref(v), ctypes.byref(nv), ctypes.byref(g), ctypes.byref(m)),
+                    "qbe_i3_shape")
+        return {"variant": v.value, "nvariants": nv.value, "grid": g.value, "m_chunks": m.value,
+                "name": self.i3_variant_name(v.value)}
+
+    def i3_variant_name(self, variant):
+        name = lib().qbe_i3_variant_name(self._h, int(variant))
+        return name.decode() if name else None
+
+    def set_i3_shape(self, variant=-1, grid=0, m_chunks=0):
+        """Set the I3 launch variant / persistent grid / m-chunks (-1, 0, 0 keep the current one)."""
+        self._check(lib().qbe_set_i3_shape(self._h, int(variant), int(grid), int(m_chunks)), "qbe_set_i3_shape")
+
+    def autotune(self):
+        """Time the I3 launch shapes on the current state and keep the fastest; returns its predicted ms."""
+        ms = _c_double()
+        self._check(lib().qbe_autotune(self._h, ctypes.byref(ms)), "qbe_autotune")
+        return ms.value
 
 
 def fd_fit_moments(rho4, mom, energy) -> QbeFermiDirac:
