@@ -71,6 +71,18 @@ const char* i3_variant_desc(int n, int prec, int variant) {
 #undef QBE_CALL
 }
 
+// Angle chunks per cell of the I1 and I2/I4 kernels: enough (cell, chunk) blocks to fill about one
+// wave of the device (3 resident 256-thread blocks per SM), at most J/2 (the I2/I4 angle pairs).
+int per_cell_chunks(int nb, int J) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int cap = 3 * (nsm > 0 ? nsm : 1);
+  int nch = (cap + nb / 2) / (nb > 0 ? nb : 1);
+  if (nch > J / 2) nch = J / 2;
+  return nch < 1 ? 1 : nch;
+}
+
 cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int prec) {
   const size_t P = (size_t)t.n * t.n;
   int dev = 0, nsm = 0;
@@ -99,7 +111,9 @@ cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int
   const size_t nparts = (size_t)nb * t.J * cw.nmc;
   cw.nparts_cap = nparts;
   cw.ws_slots = nb > cw.grid_i3 ? nb : cw.grid_i3;
+  cw.nch = per_cell_chunks(nb, t.J);
   size_t ws_fields = 6 * (size_t)nb;
+  if (5 * (size_t)nb * cw.nch > ws_fields) ws_fields = 5 * (size_t)nb * cw.nch;   // k_i24: 5 fields per block
   if (3 * (size_t)cw.grid_max > ws_fields) ws_fields = 3 * (size_t)cw.grid_max;
   cw.ws_fields = ws_fields;
   const size_t N = t.N;
@@ -113,6 +127,11 @@ cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int
   QBE_ALLOC(cw.Dacc, (size_t)nb * 2 * P * cz);
   QBE_ALLOC(cw.K2acc, (size_t)nb * P * rz);
   QBE_ALLOC(cw.K4acc, (size_t)nb * 2 * P * cz);
+  if (cw.nch > 1) {
+    QBE_ALLOC(cw.Dpart, (size_t)nb * cw.nch * 2 * P * cz);
+    QBE_ALLOC(cw.K2part, (size_t)nb * cw.nch * P * rz);
+    QBE_ALLOC(cw.K4part, (size_t)nb * cw.nch * 2 * P * cz);
+  }
   QBE_ALLOC(cw.K3part, nparts * 2 * P * cz);
   QBE_ALLOC(cw.ws, ws_fields * P * cz);
   QBE_ALLOC(cw.cbuf, (size_t)nb * 4 * N * N * sizeof(double));
@@ -123,6 +142,7 @@ cudaError_t alloc_collision_work(const Tables& t, int nb, CollisionWork& cw, int
 
 void free_collision_work(CollisionWork& cw) {
   cudaFree(cw.what); cudaFree(cw.wfine); cudaFree(cw.Dacc); cudaFree(cw.K2acc); cudaFree(cw.K4acc);
+  cudaFree(cw.Dpart); cudaFree(cw.K2part); cudaFree(cw.K4part);
   cudaFree(cw.K3part); cudaFree(cw.ws); cudaFree(cw.cbuf); cudaFree(cw.wbuf);
   cw = CollisionWork();
 }
@@ -238,6 +258,9 @@ cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec, int k
   // per-cell kernels: 7 fields per cell; I3 transpose: 7 + 2 K fields per block (staged form)
   size_t ws_fields = 7 * (size_t)nb;
   if ((7 + 2 * (size_t)kcap) * vw.grid > ws_fields) ws_fields = (7 + 2 * (size_t)kcap) * vw.grid;
+  // the recomputed forward's I2/I4 kernel: 5 fields per (cell, angle chunk) block
+  const size_t nch = (size_t)per_cell_chunks(nb, t.J);
+  if (5 * (size_t)nb * nch > ws_fields) ws_fields = 5 * (size_t)nb * nch;
   const size_t kc = (size_t)kcap;
   const size_t cz = prec == 1 ? sizeof(float2) : sizeof(double2);
   const size_t rz = cz / 2;

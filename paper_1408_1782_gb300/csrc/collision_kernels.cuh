@@ -133,19 +133,21 @@ __global__ void __launch_bounds__(kThreads) k_i1(const typename Vec2Of<T>::type*
                                                  const typename Vec2Of<T>::type* wfine, typename Vec2Of<T>::type* Dacc,
                                                  typename Vec2Of<T>::type* ws,
                                                  const typename Vec2Of<T>::type* __restrict__ gtw,
-                                                 const T* __restrict__ phip, const T* __restrict__ Ktab, int J) {
+                                                 const T* __restrict__ phip, const T* __restrict__ Ktab, int J,
+                                                 int nch) {
   using C2 = typename Vec2Of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
   C2* sm = tw + n;
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
-  const int c = blockIdx.x;
+  // block (cell c, angle chunk ch): angles j' in [J ch / nch, J (ch + 1) / nch); D partial [c][ch]
+  const int c = blockIdx.x / nch, ch = blockIdx.x % nch;
   C2* G = ws + (size_t)blockIdx.x * P;
-  C2* D = Dacc + (size_t)c * 2 * P;
+  C2* D = Dacc + (size_t)blockIdx.x * 2 * P;
   zero_fields(D, 2 * P);
   const C2* wf0 = wfine + (size_t)c * 2 * P;
-  for (int jp = 0; jp < J; ++jp) {
+  for (int jp = J * ch / nch; jp < J * (ch + 1) / nch; ++jp) {
     const T* ph = phip + (size_t)jp * P;
     const T* K = Ktab + (size_t)jp * P;
     for (int p = 0; p < 2; ++p) {
@@ -180,26 +182,28 @@ __global__ void __launch_bounds__(kThreads) k_i24(const typename Vec2Of<T>::type
                                                   const typename Vec2Of<T>::type* wfine, T* K2acc,
                                                   typename Vec2Of<T>::type* K4acc, typename Vec2Of<T>::type* ws,
                                                   const typename Vec2Of<T>::type* __restrict__ gtw,
-                                                  const T* __restrict__ psi, int J) {
+                                                  const T* __restrict__ psi, int J, int nch) {
   using C2 = typename Vec2Of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
   C2* sm = tw + n;
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
-  const int c = blockIdx.x;
+  // block (cell c, chunk ch) of the J/2 angle pairs; K2, K4 partials [c][ch]
+  const int c = blockIdx.x / nch, ch = blockIdx.x % nch;
   C2* slot = ws + (size_t)blockIdx.x * 5 * P;
   C2* FA = slot;            // [2][P]
   C2* FB = slot + 2 * P;    // [2][P]
   C2* G = slot + 4 * P;
-  T* K2 = K2acc + (size_t)c * P;
-  C2* K4 = K4acc + (size_t)c * 2 * P;
+  T* K2 = K2acc + (size_t)blockIdx.x * P;
+  C2* K4 = K4acc + (size_t)blockIdx.x * 2 * P;
   for (int i = threadIdx.x; i < P; i += blockDim.x) K2[i] = (T)0;
   zero_fields(K4, 2 * P);
   const C2* wf0 = wfine + (size_t)c * 2 * P;
   const T wj = (T)(kPi / J);
   const T scale = (T)(kPi / J / (double)P);
-  for (int j = 0; j < J / 2; ++j) {
+  const int H = J / 2;
+  for (int j = H * ch / nch; j < H * (ch + 1) / nch; ++j) {
     const int jp = j + J / 2;
     for (int p = 0; p < 2; ++p) {
       const C2* in = what + ((size_t)c * 4 + p) * P;
@@ -237,6 +241,34 @@ __global__ void __launch_bounds__(kThreads) k_i24(const typename Vec2Of<T>::type
             });
       }
     }
+  }
+}
+
+// Sum of the per-chunk partials of k_i1 (D, 2 complex fields) and k_i24 (K2 real, K4 2 complex)
+// of each cell, in chunk order: part[c][ch][...] -> acc[c][...].
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_reduce_chunks(const T* __restrict__ Dpart, const T* __restrict__ K2part,
+                                                            const T* __restrict__ K4part, T* Dacc, T* K2acc, T* K4acc,
+                                                            int nch, int ncells, size_t P) {
+  const size_t per_c = 4 * P, per_r = P;   // reals per cell: D and K4 (2 complex fields each), K2
+  const size_t total = (size_t)ncells * (2 * per_c + per_r);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const T* src;
+    T* dst;
+    size_t c, e, stride;
+    if (i < (size_t)ncells * per_c) {
+      c = i / per_c; e = i % per_c; src = Dpart; dst = Dacc; stride = per_c;
+    } else if (i < (size_t)ncells * 2 * per_c) {
+      const size_t k = i - (size_t)ncells * per_c;
+      c = k / per_c; e = k % per_c; src = K4part; dst = K4acc; stride = per_c;
+    } else {
+      const size_t k = i - (size_t)ncells * 2 * per_c;
+      c = k / per_r; e = k % per_r; src = K2part; dst = K2acc; stride = per_r;
+    }
+    const T* p = src + (c * nch) * stride + e;
+    T sum = p[0];
+    for (int ch = 1; ch < nch; ++ch) sum += p[(size_t)ch * stride];
+    dst[c * stride + e] = sum;
   }
 }
 
@@ -308,7 +340,7 @@ __global__ void __launch_bounds__(NTH, MINB)
         const C2* wa = wf + (size_t)(a >> 1) * P;
         const C2* Sa = Sig + (size_t)(a >> 1) * P;
         const bool im = (a & 1) != 0;
-        const T eta = (a == 0) ? (T)1 : (T)-1;
+        const bool pos_eta = (a == 0);
         for (int p = 0; p < 2; ++p) {
           const C2* Sp = Sig + (size_t)p * P;
           C2* accp = acc + (size_t)p * P;
@@ -326,10 +358,12 @@ __global__ void __launch_bounds__(NTH, MINB)
           row_pass<n, 1, false, 0, CB>(
               sm, tw, [&](int ix, int iy) { return G[ix * n + iy]; }, NoMid(),
               [&](int ix, int iy, C2 v) {
+                // eta_a = +1 for a = 0, -1 otherwise: the sign goes into the FMAs
                 const C2 s = Sa[ix * n + iy];
-                const T f = eta * (im ? s.y : s.x);
+                const T f = im ? s.y : s.x;
                 const C2 d = accp[ix * n + iy];
-                accp[ix * n + iy] = mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y));
+                accp[ix * n + iy] = pos_eta ? mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y))
+                                            : mk2(fmaT(-f, v.x, d.x), fmaT(-f, v.y, d.y));
               });
         }
       }
@@ -889,6 +923,36 @@ const char* i3_variant_name(int v) {
   return i3_variant<n, T>(v).name;
 }
 
+// I1 and I2/I4 of ncells cells over (cell, angle chunk) blocks (cw.nch chunks per cell), then the
+// chunk partials summed into Dacc, K2acc, K4acc (skipped with one chunk: the kernels write there).
+template <int n, class T>
+cudaError_t per_cell_terms(const Tables& t, CollisionWork& cw, typename Vec2Of<T>::type* ws, int ncells,
+                           cudaStream_t s, long long& launches, KernelTimer* tm) {
+  using C2 = typename Vec2Of<T>::type;
+  const TabPtrs<T> tb = tab_ptrs<T>(t);
+  const C2* what = (const C2*)cw.what;
+  const C2* wfine = (const C2*)cw.wfine;
+  const size_t sm = smem_bytes<n, T>();
+  const int nch = cw.nch < 1 ? 1 : cw.nch;
+  C2* D = (C2*)(nch > 1 ? cw.Dpart : cw.Dacc);
+  T* K2 = (T*)(nch > 1 ? cw.K2part : cw.K2acc);
+  C2* K4 = (C2*)(nch > 1 ? cw.K4part : cw.K4acc);
+  if (tm) tm->begin(KG_I1, s);
+  k_i1<n, T><<<ncells * nch, kThreads, sm, s>>>(what, wfine, D, ws, tb.tw, tb.phip, tb.Ktab, t.J, nch);
+  if (tm) tm->end(s);
+  if (tm) tm->begin(KG_I24, s);
+  k_i24<n, T><<<ncells * nch, kThreads, sm, s>>>(what, wfine, K2, K4, ws, tb.tw, tb.psi, t.J, nch);
+  if (nch > 1) {
+    k_reduce_chunks<T><<<(ncells * 5 * n * n + kThreads * 8 - 1) / (kThreads * 8), kThreads, 0, s>>>(
+        (const T*)cw.Dpart, (const T*)cw.K2part, (const T*)cw.K4part, (T*)cw.Dacc, (T*)cw.K2acc, (T*)cw.K4acc, nch,
+        ncells, (size_t)n * n);
+    ++launches;
+  }
+  if (tm) tm->end(s);
+  launches += 2;
+  return cudaGetLastError();
+}
+
 // The collision operator in three parts: the per-cell terms before I3 (prep, I1, I2/I4), the I3
 // launch (a work queue over the units of one or several simulations of the same padded size), and
 // the per-cell assembly.  collide_batch_n runs all three for one simulation.
@@ -907,13 +971,9 @@ cudaError_t collide_pre_n(const Tables& t, CollisionWork& cw, const double* w, i
   begin(KG_PREP);
   k_prep<n, T><<<ncells, kThreads, sm, s>>>(w, what, wfine, ws, tb.tw);
   end();
-  begin(KG_I1);
-  k_i1<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, (C2*)cw.Dacc, ws, tb.tw, tb.phip, tb.Ktab, t.J);
-  end();
-  begin(KG_I24);
-  k_i24<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, (T*)cw.K2acc, (C2*)cw.K4acc, ws, tb.tw, tb.psi, t.J);
-  end();
-  launches += 3;
+  cudaError_t e = per_cell_terms<n, T>(t, cw, ws, ncells, s, launches, tm);
+  if (e != cudaSuccess) return e;
+  ++launches;
   return cudaGetLastError();
 }
 

@@ -801,9 +801,11 @@ cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const
   auto end = [&]() { if (tm) tm->end(s); };
   begin(KG_VJP);
   k_prep<n, T><<<ncells, kThreads, sm, s>>>(w, what, wfine, ws, tb.tw);
-  k_i1<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, Dacc, ws, tb.tw, tb.phip, tb.Ktab, t.J);
-  k_i24<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, K2acc, K4acc, ws, tb.tw, tb.psi, t.J);
-  launches += 3;
+  ++launches;
+  {
+    const cudaError_t e = per_cell_terms<n, T>(t, cw, ws, ncells, s, launches, nullptr);
+    if (e != cudaSuccess) return e;
+  }
   for (int k = 0; k < K; ++k) {
     C2* nu = (C2*)vw.nu + k * c_stride;
     T* nuf = (T*)vw.nuf + k * r_stride;

@@ -213,6 +213,27 @@ __device__ __forceinline__ void dft(C2 (&a)[R]) {
   Dft<R, SIGN, C2>::run(a);
 }
 
+// DFT of length R (a power of two) of the inputs a[i] multiplied by real scales sc[i], the scaling
+// fused into the first radix-2 stage: u su +- x sx as t = x sx (one multiplication per component)
+// and two FMAs, instead of two multiplications and two additions per component.
+template <int R, int SIGN, class C2>
+__device__ __forceinline__ void dft_scaled(C2 (&a)[R], const typename RealOf<C2>::type (&sc)[R]) {
+  static_assert((R & (R - 1)) == 0 && R >= 2, "power-of-two length");
+  constexpr int L2 = ilog2c(R);
+  C2 b[R];
+#pragma unroll
+  for (int g = 0; g < R; g += 2) {
+    const int iu = bitrev(g, L2), ix = bitrev(g + 1, L2);
+    const C2 u = a[iu], x = a[ix];
+    const C2 t = mk2(x.x * sc[ix], x.y * sc[ix]);
+    b[g] = mk2(fmaT(u.x, sc[iu], t.x), fmaT(u.y, sc[iu], t.y));
+    b[g + 1] = mk2(fmaT(u.x, sc[iu], -t.x), fmaT(u.y, sc[iu], -t.y));
+  }
+  DftStage<R, SIGN, 4, C2>::run(b);
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[i] = b[i];
+}
+
 // FFT of nl lines of length n held in shared (or global) memory:
 // element e of line l at buf[l*ls + e*es].  tw[t2*A + k1] = exp(-2 pi i t2 k1 / n).
 // SIGN < 0: forward, natural -> permuted.  SIGN > 0: inverse, permuted -> natural.
@@ -302,9 +323,10 @@ __device__ __forceinline__ void fft_conv_lines(C2* buf, int nl, int ls, int es, 
 #pragma unroll
     for (int t2 = 0; t2 < B; ++t2) b[t2] = base[t2 * es];
     dft<B, -1>(b);
+    typename RealOf<C2>::type sc[B];
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) b[k2] = cscale(b[k2], (typename RealOf<C2>::type)mul(l, B * k1 + k2));
-    dft<B, 1>(b);
+    for (int k2 = 0; k2 < B; ++k2) sc[k2] = (typename RealOf<C2>::type)mul(l, B * k1 + k2);
+    dft_scaled<B, 1>(b, sc);
 #pragma unroll
     for (int t2 = 0; t2 < B; ++t2) base[t2 * es] = b[t2];
   }

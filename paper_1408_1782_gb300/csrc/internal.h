@@ -87,6 +87,10 @@ struct CollisionWork {
   void* Dacc = nullptr;      // [nb][2][n*n] spectral D (pairs (1,2), (3,-))
   void* K2acc = nullptr;     // [nb][n*n] (real)
   void* K4acc = nullptr;     // [nb][2][n*n] spectral K4 pairs (0,1), (2,3)
+  int nch = 1;               // angle chunks per cell of the I1 and I2/I4 kernels
+  void* Dpart = nullptr;     // their per-chunk partials [nb][nch][...] (nch > 1 only)
+  void* K2part = nullptr;
+  void* K4part = nullptr;
   void* K3part = nullptr;    // [nb*J*nmc][2][n*n] fine-grid K3 pair partial sums
   void* ws = nullptr;        // per-CTA scratch
   size_t ws_fields = 0;      // complex n*n fields of scratch per CTA slot
