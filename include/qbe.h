@@ -297,7 +297,8 @@ int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launc
  *   - a launch variant: one of the kernel forms instantiated for this padded
  *     grid size 2N and precision.  FP64: the staged kernel with 256 threads and
  *     64 KB shared-memory chunks (3 blocks per SM) or 128 threads and 32 KB
- *     chunks (6 per SM).  FP32-split form, 2N = 64, 96, 128: the fused
+ *     chunks (6 per SM), or the staged kernel with its global loads and
+ *     stores fused into the line stages (256 threads, 64 KB).  FP32-split form, 2N = 64, 96, 128: the fused
  *     shared-memory kernel in two thread/accumulation shapes, or the kernel
  *     whose element passes go through shared memory; 2N <= 32: the latter
  *     only; 2N = 192, 256: the cluster kernel only;

@@ -487,6 +487,7 @@ constexpr size_t i3_smem_bytes() {   // twiddles, the field (padded rows), psi'_
 }
 
 #include "i3_fused.cuh"
+#include "i3_staged_fused.cuh"
 
 // Padded sizes with the fused shared-memory FP32 kernel (whole row tasks per thread for its shapes).
 template <int n>
@@ -796,7 +797,7 @@ size_t i3_staged_smem_bytes() {
 // Launch variants of the I3 kernel for padded size n and transform type T: the shapes the
 // autotuner chooses among (i3_default_variant gives the one a new handle starts with).
 //   FP64 (every size): the staged kernel as (threads, chunk bytes, blocks per SM)
-//     0: (256, 64 KB, 3)   1: (128, 32 KB, 6)
+//     0: (256, 64 KB, 3)   1: (128, 32 KB, 6);  k_i3_sf 2: (256, 64 KB, 3)   3: (128, 32 KB, 6)
 //   FP32, n = 64, 96, 128: 0, 1, 2: the fused shared-memory kernel in the FusedShapes<n> shapes,
 //     3: k_i3_smem (1024 threads, element passes through shared memory)
 //   FP32, n <= 32: k_i3_smem;  FP32, n > 128: the cluster kernel.
@@ -815,7 +816,7 @@ constexpr int i3_nvariants() {
     else if constexpr (use_i3_fused<n>()) return 4;
     else return 1;
   } else {
-    return 2;
+    return 4;
   }
 }
 
@@ -843,6 +844,12 @@ I3Launch i3_variant(int v) {
     if (v == 1)
       l = {(const void*)k_i3<n, T, 128, 32768, 6>, 128, i3_staged_smem_bytes<n, T, 32768>(), false,
            "staged, 128 threads, 32 KB chunks"};
+    else if (v == 2)
+      l = {(const void*)k_i3_sf<n, T, 256, 65536, 3>, 256, i3_sf_smem_bytes<n, T, 65536>(), false,
+           "staged with fused loads and stores, 256 threads, 64 KB chunks"};
+    else if (v == 3)
+      l = {(const void*)k_i3_sf<n, T, 128, 32768, 6>, 128, i3_sf_smem_bytes<n, T, 32768>(), false,
+           "staged with fused loads and stores, 128 threads, 32 KB chunks"};
     else
       l = {(const void*)k_i3<n, T, 256, 65536, 3>, 256, i3_staged_smem_bytes<n, T, 65536>(), false,
            "staged, 256 threads, 64 KB chunks"};
@@ -910,10 +917,14 @@ int i3_variant_count() {
   return i3_nvariants<n, T>();
 }
 
-// The variant a new handle starts with (the fastest measured on a GB300 for this size).
+// The variant a new handle starts with (the fastest measured on a GB300 for this size).  FP64, I3
+// launch in ms for variants 0..3 (J = M = 32): N = 16, 128 cells 136.8 136.2 132.9 129.4;
+// N = 32, 128 cells 652.2 640.5 625.3 630.4; N = 48, 64 cells 868.4 886.2 860.3 879.5; N = 64,
+// 32 cells 752.1 760.2 732.5 742.2; N = 128, 8 cells 897.0 902.9 885.5 901.9.
 template <int n, class T>
 int i3_default_variant() {
   if constexpr (std::is_same<T, float>::value && use_i3_fused<n>()) return FusedShapes<n>::DEFAULT;
+  else if constexpr (std::is_same<T, double>::value) return 2;
   else return 0;
 }
 

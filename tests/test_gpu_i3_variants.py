@@ -41,12 +41,12 @@ def _collide_all_variants(q, w, N, J, M, prec):
     return out
 
 
-@pytest.mark.parametrize("N,J,M,ncells", [(16, 8, 6, 3), (64, 4, 3, 2)])
+@pytest.mark.parametrize("N,J,M,ncells", [(16, 8, 6, 3), (48, 4, 2, 1), (64, 4, 3, 2)])
 def test_fp64_variants_match_oracle(qbe, N, J, M, ncells):
     w = inputs.synthetic_w(N, ncells, seed=40 + N, perturb=0.05)
     ref = O.collision(w, O.Params(N=N, J=J, M=M))
     res = _collide_all_variants(qbe, w, N, J, M, 0)
-    assert len(res) == 2
+    assert len(res) == 4
     for v, got in res.items():
         assert np.abs(got - ref).max() < TOL_F64 * np.abs(ref).max(), v
 
