@@ -1,18 +1,18 @@
 // I3 (Hu-Ying term, eq. approxH-JM) for fields larger than one block's shared memory (the FP64 form):
-// the staged kernel's row and column passes over chunks of RC rows / CC columns, with the global
-// loads and stores of each convolution fused into the line stages that touch the natural
-// (real-space) order.  Included by collision_kernels.cuh inside its anonymous namespace.
+// staged row and column passes over chunks of RC rows / CC lines, with every global load and store
+// of a convolution fused into a line stage.  Included by collision_kernels.cuh inside its anonymous
+// namespace.
 //
-// Per convolution (a, p) of a unit's m, as in k_i3:
-//   row pass, forward:  stage A loads w_a Sigma_p (tasks (row, t2), t2-fastest: coalesced), stage B,
-//                       the chunk copied to the block's field G in global memory;
-//   column pass:        stage A loads its columns of G (tasks column-fastest: coalesced), stage B
-//                       with the psi'_j multiplier between forward and inverse, stage A writes back;
-//   row pass, inverse:  G's rows copied in, stage B, stage A multiplies by eta_a S_a and accumulates
-//                       into the unit's partial sum.
-// The staged k_i3 moves each chunk through separate element loops around every pass (load into
-// shared memory, transform, store); here only the two copies at the permuted-order side remain, so
-// a pass has fewer barriers and phases without floating-point work.
+// The block's scratch field between the passes is stored transposed, G'[ky][x] (ky in the row
+// transform's permuted order), so that each pass reads and writes it with coalesced accesses
+// straight from its line stages:
+//   row pass, forward:  stage A loads w_a Sigma_p (tasks (row, t2), t2-fastest), stage B stores its
+//                       B spectral values of a row into B lines of G' (lanes = consecutive rows);
+//   line pass (x):      stage A loads a line of G' (contiguous in x), stage B with the psi'_j
+//                       multiplier between forward and inverse, stage A stores the line back;
+//   row pass, inverse:  stage B loads B lines of G' at its row (lanes = consecutive rows), stage A
+//                       multiplies by eta_a S_a and accumulates into the unit's partial sum.
+// Shared memory holds one chunk at a time; no pass copies a chunk through it without transforming.
 #pragma once
 
 template <int n, class T, int NTH, int CB, int MINB>
@@ -24,7 +24,8 @@ __global__ void __launch_bounds__(NTH, MINB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);   // tw[t2 A + k1]
   C2* twT = tw + n;                           // twT[k1 B + t2] = tw[t2 A + k1] (t2-fastest lanes)
-  C2* sm = twT + n;                           // one chunk: [RC][LS] rows or [n][CC] columns
+  C2* sm = twT + n;                           // one chunk: [RC][LS] rows, or [CC][LS] lines of G'
+  static_assert(RC == CC, "row and line chunks share the buffer");
   __shared__ int xcols[n];
   __shared__ unsigned char xmask[n];
   if (threadIdx.x == 0) {
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(NTH, MINB)
   const int tid = threadIdx.x;
   C2* slot = ws + (size_t)blockIdx.x * 3 * P;
   C2* Sig = slot;           // [2][P]
-  C2* G = slot + 2 * P;
+  C2* G = slot + 2 * P;     // G'[ky][x] between the passes
   for (int gunit = blockIdx.x; gunit < jobs.total; gunit += gridDim.x) {
     const I3Job<T>& jb = jobs.job[i3_job_of(jobs, gunit)];
     const int unit = gunit - jb.unit_begin;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(NTH, MINB)
         for (int p = 0; p < 2; ++p) {
           const C2* Sp = Sig + (size_t)p * P;
           C2* accp = acc + (size_t)p * P;
-          // ---- row pass, forward ----
+          // ---- row pass, forward: rows r0..r0+RC into lines of G' ----
           for (int r0 = 0; r0 < n; r0 += RC) {
             for (int task = tid; task < RC * B; task += NTH) {
               const int r = task / B, t2 = task % B, row = r0 + r;
@@ -99,78 +100,66 @@ __global__ void __launch_bounds__(NTH, MINB)
             __syncthreads();
             for (int task = tid; task < RC * A; task += NTH) {
               const int r = task % RC, k1 = task / RC;
-              C2* base = sm + r * LS + B * k1;
+              const C2* base = sm + r * LS + B * k1;
               C2 b[B];
 #pragma unroll
               for (int t = 0; t < B; ++t) b[t] = base[t];
               dft<B, -1>(b);
 #pragma unroll
-              for (int t = 0; t < B; ++t) base[t] = b[t];
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int idx = tid; idx < RC * n; idx += NTH) {
-              const int r = idx / n, iy = idx % n;
-              G[(r0 + r) * n + iy] = sm[r * LS + iy];
+              for (int t = 0; t < B; ++t) G[(B * k1 + t) * n + r0 + r] = b[t];
             }
             __syncthreads();
           }
-          // ---- column pass: forward, psi'_j, inverse ----
+          // ---- line pass along x: forward, psi'_j, inverse on lines c0..c0+CC of G' ----
           for (int c0 = 0; c0 < n; c0 += CC) {
             for (int task = tid; task < CC * B; task += NTH) {
-              const int cc = task % CC, t2 = task / CC;
+              const int cc = task / B, t2 = task % B;
               C2 v[A];
 #pragma unroll
-              for (int t1 = 0; t1 < A; ++t1) v[t1] = G[(B * t1 + t2) * n + c0 + cc];
+              for (int t1 = 0; t1 < A; ++t1) v[t1] = G[(c0 + cc) * n + B * t1 + t2];
               dft<A, -1>(v);
 #pragma unroll
-              for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[t2 * A + k1]);
+              for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], twT[k1 * B + t2]);
 #pragma unroll
-              for (int k1 = 0; k1 < A; ++k1) sm[(B * k1 + t2) * CC + cc] = v[k1];
+              for (int k1 = 0; k1 < A; ++k1) sm[cc * LS + B * k1 + t2] = v[k1];
             }
             __syncthreads();
             for (int task = tid; task < CC * A; task += NTH) {
               const int cc = task % CC, k1 = task / CC;
-              C2* base = sm + B * k1 * CC + cc;
+              C2* base = sm + cc * LS + B * k1;
               C2 b[B];
 #pragma unroll
-              for (int t = 0; t < B; ++t) b[t] = base[t * CC];
+              for (int t = 0; t < B; ++t) b[t] = base[t];
               dft<B, -1>(b);
               T sc[B];
 #pragma unroll
               for (int t = 0; t < B; ++t) sc[t] = psp[(B * k1 + t) * n + c0 + cc];
               dft_scaled<B, 1>(b, sc);
 #pragma unroll
-              for (int t = 0; t < B; ++t) base[t * CC] = b[t];
+              for (int t = 0; t < B; ++t) base[t] = b[t];
             }
             __syncthreads();
             for (int task = tid; task < CC * B; task += NTH) {
-              const int cc = task % CC, t2 = task / CC;
+              const int cc = task / B, t2 = task % B;
               C2 v[A];
 #pragma unroll
-              for (int k1 = 0; k1 < A; ++k1) v[k1] = sm[(B * k1 + t2) * CC + cc];
+              for (int k1 = 0; k1 < A; ++k1) v[k1] = sm[cc * LS + B * k1 + t2];
 #pragma unroll
-              for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], tw[t2 * A + k1]);
+              for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2]);
               dft<A, 1>(v);
 #pragma unroll
-              for (int t1 = 0; t1 < A; ++t1) G[(B * t1 + t2) * n + c0 + cc] = v[t1];
+              for (int t1 = 0; t1 < A; ++t1) G[(c0 + cc) * n + B * t1 + t2] = v[t1];
             }
             __syncthreads();
           }
           // ---- row pass, inverse, accumulated with eta_a S_a ----
           for (int r0 = 0; r0 < n; r0 += RC) {
-#pragma unroll 4
-            for (int idx = tid; idx < RC * n; idx += NTH) {
-              const int r = idx / n, iy = idx % n;
-              sm[r * LS + iy] = G[(r0 + r) * n + iy];
-            }
-            __syncthreads();
             for (int task = tid; task < RC * A; task += NTH) {
               const int r = task % RC, k1 = task / RC;
               C2* base = sm + r * LS + B * k1;
               C2 b[B];
 #pragma unroll
-              for (int t = 0; t < B; ++t) b[t] = base[t];
+              for (int t = 0; t < B; ++t) b[t] = G[(B * k1 + t) * n + r0 + r];
               dft<B, 1>(b);
 #pragma unroll
               for (int t = 0; t < B; ++t) base[t] = b[t];
@@ -203,7 +192,7 @@ __global__ void __launch_bounds__(NTH, MINB)
 }
 
 template <int n, class T, int CB>
-constexpr size_t i3_sf_smem_bytes() {   // twiddles (two orders) and one chunk
+constexpr size_t i3_sf_smem_bytes() {   // twiddles (two orders) and one chunk of RC padded lines
   using C2 = typename Vec2Of<T>::type;
-  return (size_t)(2 * n + Chunk<n, sizeof(C2), CB>::SMEM_ELEMS) * sizeof(C2);
+  return (size_t)(2 * n + Chunk<n, sizeof(C2), CB>::RC * Chunk<n, sizeof(C2), CB>::LS) * sizeof(C2);
 }
