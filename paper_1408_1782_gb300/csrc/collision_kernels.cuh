@@ -515,14 +515,16 @@ template <> struct FusedShapes<128> {
 // CTA r holds rows [r R, r R + R) of the transform field (R = n / kI3Cluster) for the row
 // transforms and columns [r R, r R + R) for the column psi' convolution, with the angle's psi'
 // columns in shared memory.  The transposes between the two go through the cluster's field in
-// global memory, ordered by cluster barriers; per cluster that field and the two shifted fields
+// global memory, stored transposed (G'[ky][x]) so that the line stages load and store it directly,
+// coalesced, ordered by cluster barriers; per cluster that field and the two shifted fields
 // (3 n^2 complex values) stay L2-resident, where 152 independent units of the staged kernel
-// (about 2.5 MB each) would not.  Same units, line transforms and accumulation order as k_i3,
-// so the results are bitwise identical.  Every CTA of a cluster runs the same loop trip counts,
-// so every barrier is reached by all of them (hardware barriers, no spin waits).
+// (about 2.5 MB each) would not.  Same units and line transforms as k_i3.  Every CTA of a cluster
+// runs the same loop trip counts, so every barrier is reached by all of them (hardware barriers,
+// no spin waits).
 // --------------------------------------------------------------------------
-// Measured at N = 128 (32 cells, C[W] I3 launch): 4 CTAs x 1024 threads 239.9 ms; 8 CTAs x 512
-// threads (two CTAs of different clusters per SM) 255.4 ms; the staged k_i3 294.5 ms.
+// Measured at N = 128 (32 cells, C[W] I3 launch), element passes through shared memory around
+// every global access: 4 CTAs x 1024 threads 239.9 ms; 8 CTAs x 512 threads (two CTAs of
+// different clusters per SM) 255.4 ms; the staged k_i3 294.5 ms.
 constexpr int kI3Cluster = 4;             // CTAs per cluster
 constexpr int kThreadsI3Cluster = 1024;   // threads per CTA
 
@@ -538,8 +540,8 @@ __host__ __device__ constexpr int i3_cluster_slab() {   // complex elements of t
 }
 
 template <int n>
-constexpr size_t i3_cluster_smem_bytes() {   // twiddles, the slab, psi' columns
-  return (size_t)(n + i3_cluster_slab<n>()) * sizeof(float2) + (size_t)n * (n / kI3Cluster) * sizeof(float);
+constexpr size_t i3_cluster_smem_bytes() {   // twiddles (two orders), the slab, psi' columns
+  return (size_t)(2 * n + i3_cluster_slab<n>()) * sizeof(float2) + (size_t)n * (n / kI3Cluster) * sizeof(float);
 }
 
 __device__ __forceinline__ int cluster_rank() {
@@ -575,8 +577,9 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3C
   static_assert(n % kI3Cluster == 0 && (n / 2) % kI3Cluster == 0, "cluster split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
-  C2* F = tw + n;                                    // [R][LS] row slab, [n][R] or [n][XC] column slab
-  float* psl = reinterpret_cast<float*>(F + i3_cluster_slab<n>());   // psi'_j of this CTA's columns, [n][R]
+  C2* twT = tw + n;                                  // twT[k1 B + t2] = tw[t2 A + k1] (t2-fastest lanes)
+  C2* F = twT + n;                                   // [R][LS] row or line slab, [n][XC] shift column slab
+  float* psl = reinterpret_cast<float*>(F + i3_cluster_slab<n>());   // psi'_j of this CTA's lines, [n][R]
   __shared__ int xcols[n];
   __shared__ unsigned char xmask[n];
   if (threadIdx.x == 0) {
@@ -588,6 +591,8 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3C
       if (in) xcols[cnt++] = pos;
     }
   }
+  for (int pos = threadIdx.x; pos < n; pos += blockDim.x)
+    twT[(pos % Split<n>::A) * Split<n>::B + pos / Split<n>::A] = gtw[pos];
   load_twiddles<n>(tw, gtw);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int rank = cluster_rank();
@@ -646,46 +651,113 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3C
         for (int idx = tid; idx < R * n; idx += nt) S[idx] = F[(idx / n) * LS + idx % n];
         __syncthreads();
       }
-      // from here on this CTA reads only its own rows of the shifted fields
+      // from here on this CTA reads only its own rows of the shifted fields.  Between the passes the
+      // cluster's field is stored transposed, Gs'[ky][x] (ky in the row transform's permuted order):
+      // the row passes reach it from stage B (lanes = consecutive rows of this CTA) and the line pass
+      // from stage A (contiguous in x), so every global access is inside a line stage and coalesced.
+      constexpr int A = Split<n>::A, B = Split<n>::B;
       for (int a = 0; a < 4; ++a) {
         const C2* wa = wf + (size_t)(a >> 1) * P + (size_t)r0 * n;
         const C2* Sa = Sig + (size_t)(a >> 1) * P + (size_t)r0 * n;
         const bool im = (a & 1) != 0;
-        const float eta = (a == 0) ? 1.f : -1.f;
+        const bool pos_eta = (a == 0);   // eta_a = +1 for a = 0, -1 otherwise
         for (int p = 0; p < 2; ++p) {
           const C2* Sp = Sig + (size_t)p * P + (size_t)r0 * n;
           C2* accp = acc + (size_t)p * P + (size_t)r0 * n;
-          // forward row transforms of w_a S_pair on this CTA's rows
-#pragma unroll 4
-          for (int idx = tid; idx < R * n; idx += nt) {
-            const C2 z = wa[idx];
-            F[(idx / n) * LS + idx % n] = cscale(Sp[idx], im ? z.y : z.x);
+          // forward row transforms of w_a S_pair on this CTA's rows: stage A loads the product
+          for (int task = tid; task < R * B; task += nt) {
+            const int r = task / B, t2 = task % B;
+            C2 v[A];
+#pragma unroll
+            for (int t1 = 0; t1 < A; ++t1) {
+              const int idx = r * n + B * t1 + t2;
+              const C2 z = wa[idx];
+              v[t1] = cscale(Sp[idx], im ? z.y : z.x);
+            }
+            dft<A, -1>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], twT[k1 * B + t2]);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) F[r * LS + B * k1 + t2] = v[k1];
           }
           __syncthreads();
-          fft_lines<n, -1>(F, R, LS, 1, tw);
-#pragma unroll 4
-          for (int idx = tid; idx < R * n; idx += nt) Gs[(size_t)r0 * n + idx] = F[(idx / n) * LS + idx % n];
+          for (int task = tid; task < R * A; task += nt) {
+            const int r = task % R, k1 = task / R;
+            C2 b[B];
+#pragma unroll
+            for (int t = 0; t < B; ++t) b[t] = F[r * LS + B * k1 + t];
+            dft<B, -1>(b);
+#pragma unroll
+            for (int t = 0; t < B; ++t) Gs[(size_t)(B * k1 + t) * n + r0 + r] = b[t];
+          }
           cluster_sync_global();                     // all rows transformed
-          // column psi' convolution on this CTA's columns
-#pragma unroll 4
-          for (int idx = tid; idx < n * R; idx += nt) F[idx] = __ldcg(&Gs[(idx / R) * n + r0 + idx % R]);
+          // psi' convolution along x on this CTA's lines ky in [r0, r0 + R)
+          for (int task = tid; task < R * B; task += nt) {
+            const int cc = task / B, t2 = task % B;
+            C2 v[A];
+#pragma unroll
+            for (int t1 = 0; t1 < A; ++t1) v[t1] = __ldcg(&Gs[(size_t)(r0 + cc) * n + B * t1 + t2]);
+            dft<A, -1>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], twT[k1 * B + t2]);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) F[cc * LS + B * k1 + t2] = v[k1];
+          }
           __syncthreads();
-          fft_conv_lines<n>(F, R, 1, R, tw, [&](int l, int pos) { return psl[pos * R + l]; });
-#pragma unroll 4
-          for (int idx = tid; idx < n * R; idx += nt) Gs[(idx / R) * n + r0 + idx % R] = F[idx];
-          cluster_sync_global();                     // all columns convolved
-          // inverse row transforms on this CTA's rows, accumulated with eta_a S_a
-#pragma unroll 4
-          for (int idx = tid; idx < R * n; idx += nt) F[(idx / n) * LS + idx % n] = __ldcg(&Gs[(size_t)r0 * n + idx]);
+          for (int task = tid; task < R * A; task += nt) {
+            const int cc = task % R, k1 = task / R;
+            C2 b[B];
+#pragma unroll
+            for (int t = 0; t < B; ++t) b[t] = F[cc * LS + B * k1 + t];
+            dft<B, -1>(b);
+            float sc[B];
+#pragma unroll
+            for (int t = 0; t < B; ++t) sc[t] = psl[(B * k1 + t) * R + cc];
+            dft_scaled<B, 1>(b, sc);
+#pragma unroll
+            for (int t = 0; t < B; ++t) F[cc * LS + B * k1 + t] = b[t];
+          }
           __syncthreads();
-          fft_lines<n, 1>(F, R, LS, 1, tw);
-#pragma unroll 4
-          for (int idx = tid; idx < R * n; idx += nt) {
-            const C2 v = F[(idx / n) * LS + idx % n];
-            const C2 sv = Sa[idx];
-            const float f = eta * (im ? sv.y : sv.x);
-            const C2 d = accp[idx];
-            accp[idx] = mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y));
+          for (int task = tid; task < R * B; task += nt) {
+            const int cc = task / B, t2 = task % B;
+            C2 v[A];
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) v[k1] = F[cc * LS + B * k1 + t2];
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2]);
+            dft<A, 1>(v);
+#pragma unroll
+            for (int t1 = 0; t1 < A; ++t1) Gs[(size_t)(r0 + cc) * n + B * t1 + t2] = v[t1];
+          }
+          cluster_sync_global();                     // all lines convolved
+          // inverse row transforms on this CTA's rows: stage B loads, stage A accumulates eta_a S_a
+          for (int task = tid; task < R * A; task += nt) {
+            const int r = task % R, k1 = task / R;
+            C2 b[B];
+#pragma unroll
+            for (int t = 0; t < B; ++t) b[t] = __ldcg(&Gs[(size_t)(B * k1 + t) * n + r0 + r]);
+            dft<B, 1>(b);
+#pragma unroll
+            for (int t = 0; t < B; ++t) F[r * LS + B * k1 + t] = b[t];
+          }
+          __syncthreads();
+          for (int task = tid; task < R * B; task += nt) {
+            const int r = task / B, t2 = task % B;
+            C2 v[A];
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) v[k1] = F[r * LS + B * k1 + t2];
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2]);
+            dft<A, 1>(v);
+#pragma unroll
+            for (int t1 = 0; t1 < A; ++t1) {
+              const int idx = r * n + B * t1 + t2;
+              const C2 sv = Sa[idx];
+              const float f = im ? sv.y : sv.x;
+              const C2 d = accp[idx];
+              accp[idx] = pos_eta ? mk2(fmaT(f, v[t1].x, d.x), fmaT(f, v[t1].y, d.y))
+                                  : mk2(fmaT(-f, v[t1].x, d.x), fmaT(-f, v[t1].y, d.y));
+            }
           }
           __syncthreads();
         }
