@@ -47,10 +47,10 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (an issue-rate microbenchmark)
 FP32_FMA_PER_CLK_PER_SM = 128        # measured 116 FFMA/clk/SM
-# DRAM bytes (read + write) per (cell, j, m) unit of the I3 kernel from one ncu capture of a slice of
-# the current kernel (8 cells at N = 64 in FP64 and FP32, 4 cells at N = 128 in FP32), scaled by units;
-# absent for sizes with no capture of the current kernel.
-I3_DRAM_BYTES_PER_UNIT = {(64, 0): 119.85e9 / 8192, (64, 1): 5.548e9 / 8192, (128, 1): 29.669e9 / 4096}
+# DRAM bytes (read + write) per (cell, j, m) unit of the default I3 kernel from one ncu capture of a
+# slice (8 cells at N = 64: k_i3_sf in FP64, k_i3_fused in FP32; 4 cells at N = 128: k_i3_cluster),
+# scaled by units; absent for sizes with no capture of the current kernel.
+I3_DRAM_BYTES_PER_UNIT = {(64, 0): 113.540e9 / 8192, (64, 1): 3.228e9 / 8192, (128, 1): 28.305e9 / 4096}
 
 
 def workload(name="plain_fp64_n64", precision=None):
@@ -375,8 +375,8 @@ def run_ours(args):
             "dtype": "f64" if prec == 0 else "f32-split",
             "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)",
             "config": config_dict(wl, world),
-            "roofline": {"kernel": ("k_i3" if prec == 0 else ("k_i3_smem" if N <= 64 else "k_i3_cluster"))
-                                   + " (Hu-Ying I3 term)", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": s.i3_shape()["name"] + " I3 kernel (Hu-Ying term)", "bound": "alu",
+                         "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": (I3_DRAM_BYTES_PER_UNIT[(N, prec)] * Nx * wl["J"] * wl["M"]
                                      if (N, prec) in I3_DRAM_BYTES_PER_UNIT else None),
@@ -485,8 +485,9 @@ def measure_forms(args, wl, W0, s64, fp64_ms_per_step, local):
         "steps": steps, "warmup": args.warmup, "ms_per_step": t_ms / steps, "steps_per_s": 1e3 * steps / t_ms,
         "speedup_vs_fp64_gpu_step": fp64_ms_per_step / (t_ms / steps),
         "error": err,
-        "roofline": {"kernel": "k_i3_smem (Hu-Ying I3 term, FP32)", "bound": "alu", "achieved": achieved,
-                     "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
+        "roofline": {"kernel": s.i3_shape()["name"] + " I3 kernel (Hu-Ying term, FP32)", "bound": "alu",
+                     "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
+                     "traffic": I3_DRAM_BYTES_PER_UNIT[(64, 1)] * Nx * wl["J"] * wl["M"] if N == 64 else None,
                      "avg_launch_ms": avg_i3 * 1e3,
                      "peak_source": f"derived: {SM_COUNT} SMs x {FP32_FMA_PER_CLK_PER_SM} FP32 FMA/clk x 2 flop x "
                                     f"{sm_max:.0f} MHz"},
@@ -583,23 +584,42 @@ def run_batched(args, local, full=False):
         desc.append(f"{N}/{Nx}/{bc[0]}")
         units += 2 * Nx * N * N
     b = qbe.Batch(sims, stream=stream)
-    shapes = b.autotune() if not full else []
     dt = 0.005
-    b.step(dt, args.warmup)            # first call captures the graph
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(dt, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_ms = e0.elapsed_time(e1)
+
+    def timed_steps():
+        b.step(dt, args.warmup)            # the first call captures the graph
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    states = [s.get_state() for s in sims]
+    untuned_ms = None
+    if args.compare_untuned:
+        untuned_ms = timed_steps() / args.steps
+        for s, W in zip(sims, states):
+            s.set_state(W)
+    t0 = time.perf_counter()
+    shapes = b.autotune()
+    tune_s = time.perf_counter() - t0
+    groups = {}
+    for s, (gg, mm, ms) in zip(sims, shapes):
+        sh = s.i3_shape()
+        groups.setdefault((s.N, s.precision), {"N": s.N, "variant": sh["name"], "grid": gg, "m_chunks": mm,
+                                               "predicted_i3_ms": round(ms, 3), "sims": 0})["sims"] += 1
+    t_ms = timed_steps()
     line = {"workload": "batched_64" if full else "batched_16", "metric": "C[W] cell·k-pts/s",
             "value": units * args.steps / (t_ms * 1e-3),
             "unit": "cell·k-pts/s", "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "untuned_ms_per_step": untuned_ms, "autotune_s": round(tune_s, 2),
             "dtype": "f32-split", "graph_launches_per_step": 1,
-            "sims": desc, "tuned_i3_shapes": [[gg, mm, round(ms, 3)] for gg, mm, ms in shapes],
+            "sims": desc, "tuned_i3_shapes": list(groups.values()),
             "note": ("the batching configuration: 64 simulations, N from {32,48,64,96,128}, Nx from [16,256], "
-                     "mixed walls, random |B| <= 1, default launch shapes" if full else
+                     "mixed walls, random |B| <= 1; one I3 work-queue launch per padded size, its launch shape "
+                     "chosen by qbe_batch_autotune" if full else
                      "16 simulations drawn from the batching configuration's distributions with N in {32,48,64} "
                      "and Nx in [16,64]; --workload batched_64 runs the full 64-simulation mix")}
     print(json.dumps(line), flush=True)
@@ -903,6 +923,8 @@ def main():
     ap.add_argument("--i3-variant", type=int, default=-1,
                     help="--mode collide: I3 launch variant (qbe_set_i3_shape); default: the library's")
     ap.add_argument("--autotune", action="store_true", help="--mode collide: run qbe_autotune first")
+    ap.add_argument("--compare-untuned", action="store_true",
+                    help="batched workloads: also time the steps with the default launch shapes first")
     ap.add_argument("--cotangents", type=int, default=1,
                     help="--mode vjp: products per call at the same state (shared transforms, up to 4 per group)")
     args = ap.parse_args()
