@@ -258,9 +258,10 @@ cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec, int k
   // per-cell kernels: 7 fields per cell; I3 transpose: 7 + 2 K fields per block (staged form)
   size_t ws_fields = 7 * (size_t)nb;
   if ((7 + 2 * (size_t)kcap) * vw.grid > ws_fields) ws_fields = (7 + 2 * (size_t)kcap) * vw.grid;
-  // the recomputed forward's I2/I4 kernel: 5 fields per (cell, angle chunk) block
+  // per (cell, angle chunk) block: the recomputed forward's I2/I4 kernel 5 fields, the I2/I4
+  // transpose 7
   const size_t nch = (size_t)per_cell_chunks(nb, t.J);
-  if (5 * (size_t)nb * nch > ws_fields) ws_fields = 5 * (size_t)nb * nch;
+  if (7 * (size_t)nb * nch > ws_fields) ws_fields = 7 * (size_t)nb * nch;
   const size_t kc = (size_t)kcap;
   const size_t cz = prec == 1 ? sizeof(float2) : sizeof(double2);
   const size_t rz = cz / 2;

@@ -141,23 +141,30 @@ __global__ void __launch_bounds__(kThreads) k_i1_vjp(
     const typename Vec2Of<T>::type* what, const typename Vec2Of<T>::type* wfine,
     const typename Vec2Of<T>::type* muD, typename Vec2Of<T>::type* nu, T* nuf, typename Vec2Of<T>::type* ws,
     const typename Vec2Of<T>::type* __restrict__ gtw, const T* __restrict__ phip, const T* __restrict__ Ktab,
-    int J) {
+    int J, int nch) {
   using C2 = typename Vec2Of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
   C2* sm = tw + n;
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
-  const int c = blockIdx.x;
+  // block (cell c, angle chunk ch); with nch > 1, nu and nuf are per-(cell, chunk) partials (zeroed
+  // here, completed by k_i24_vjp, summed by k_add_chunks), with nch = 1 the cell's own accumulators
+  const int c = blockIdx.x / nch, ch = blockIdx.x % nch;
   C2* slot = ws + (size_t)blockIdx.x * 3 * P;
   C2* Aw = slot;          // A w_pair
   C2* Bm = slot + P;      // K' mu_pair
   C2* G = slot + 2 * P;
   const C2* wf0 = wfine + (size_t)c * 2 * P;
-  C2* nuc = nu + (size_t)c * 2 * P;
-  T* nufc = nuf + (size_t)c * P;
+  C2* nuc = nu + (size_t)blockIdx.x * 2 * P;
+  T* nufc = nuf + (size_t)blockIdx.x * P;
+  if (nch > 1) {
+    zero_fields(nuc, 2 * P);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) nufc[i] = (T)0;
+    __syncthreads();
+  }
   const T invP = (T)(1.0 / (double)P);
-  for (int jp = 0; jp < J; ++jp) {
+  for (int jp = J * ch / nch; jp < J * (ch + 1) / nch; ++jp) {
     const T* ph = phip + (size_t)jp * P;
     const T* K = Ktab + (size_t)jp * P;
     for (int p = 0; p < 2; ++p) {
@@ -221,14 +228,15 @@ template <int n, class T>
 __global__ void __launch_bounds__(kThreads) k_i24_vjp(
     const typename Vec2Of<T>::type* what, const typename Vec2Of<T>::type* wfine, const T* muK2,
     const typename Vec2Of<T>::type* mu4, typename Vec2Of<T>::type* nu, T* nuf, typename Vec2Of<T>::type* ws,
-    const typename Vec2Of<T>::type* __restrict__ gtw, const T* __restrict__ psi, int J) {
+    const typename Vec2Of<T>::type* __restrict__ gtw, const T* __restrict__ psi, int J, int nch) {
   using C2 = typename Vec2Of<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
   C2* sm = tw + n;
   load_twiddles<n>(tw, gtw);
   constexpr int P = n * n;
-  const int c = blockIdx.x;
+  // block (cell c, chunk ch of the J/2 angle pairs); nu, nuf as in k_i1_vjp
+  const int c = blockIdx.x / nch, ch = blockIdx.x % nch;
   C2* slot = ws + (size_t)blockIdx.x * 7 * P;
   C2* FA = slot;             // [2] F_{.,j}
   C2* FB = slot + 2 * P;     // [2] F_{.,j'}
@@ -237,11 +245,12 @@ __global__ void __launch_bounds__(kThreads) k_i24_vjp(
   const C2* wf0 = wfine + (size_t)c * 2 * P;
   const T* mk2c = muK2 + (size_t)c * P;
   const C2* m4 = mu4 + (size_t)c * 2 * P;
-  C2* nuc = nu + (size_t)c * 2 * P;
-  T* nufc = nuf + (size_t)c * P;
+  C2* nuc = nu + (size_t)blockIdx.x * 2 * P;
+  T* nufc = nuf + (size_t)blockIdx.x * P;
   const T wj = (T)(kPi / J);
   const T invP = (T)(1.0 / (double)P);
-  for (int j = 0; j < J / 2; ++j) {
+  const int H = J / 2;
+  for (int j = H * ch / nch; j < H * (ch + 1) / nch; ++j) {
     const int jq = j + J / 2;
     for (int p = 0; p < 2; ++p) {
       const C2* in = what + ((size_t)c * 4 + p) * P;
@@ -318,6 +327,30 @@ __global__ void __launch_bounds__(kThreads) k_i24_vjp(
             });
       }
     }
+  }
+}
+
+// nu[c] += sum_ch nupart[c][ch] (2 complex fields) and nuf[c] += sum_ch nufpart[c][ch] (1 real
+// field), in chunk order: the per-(cell, chunk) partials of k_i1_vjp + k_i24_vjp.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_add_chunks(const T* __restrict__ nupart, const T* __restrict__ nufpart,
+                                                         T* nu, T* nuf, int nch, int ncells, size_t P) {
+  const size_t per_c = 4 * P;
+  const size_t total = (size_t)ncells * (per_c + P);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const T* src;
+    T* dst;
+    size_t c, e, stride;
+    if (i < (size_t)ncells * per_c) {
+      c = i / per_c; e = i % per_c; src = nupart; dst = nu; stride = per_c;
+    } else {
+      const size_t k = i - (size_t)ncells * per_c;
+      c = k / P; e = k % P; src = nufpart; dst = nuf; stride = P;
+    }
+    const T* p = src + (c * nch) * stride + e;
+    T sum = p[0];
+    for (int ch = 1; ch < nch; ++ch) sum += p[(size_t)ch * stride];
+    dst[c * stride + e] += sum;
   }
 }
 
@@ -815,9 +848,22 @@ cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const
     C2* mu3 = (C2*)vw.mu3 + k * c_stride;
     k_vjp_seed<n, T><<<ncells, kThreads, sm, s>>>(lam[k], wfine, Dacc, K2acc, K4acc, nu, nuf, muD, muK2, mu4, mu3,
                                                   ws, tb.tw);
-    k_i1_vjp<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, muD, nu, nuf, ws, tb.tw, tb.phip, tb.Ktab, t.J);
-    k_i24_vjp<n, T><<<ncells, kThreads, sm, s>>>(what, wfine, muK2, mu4, nu, nuf, ws, tb.tw, tb.psi, t.J);
+    // I1 and I2/I4 transposes over (cell, angle chunk) blocks; their per-chunk cotangents go to the
+    // forward's chunk-partial buffers (free once per_cell_terms has reduced them) and are summed in
+    // chunk order into nu and nuf
+    const int nch = cw.nch < 1 ? 1 : cw.nch;
+    C2* nup = nch > 1 ? (C2*)cw.Dpart : nu;
+    T* nufp = nch > 1 ? (T*)cw.K2part : nuf;
+    k_i1_vjp<n, T><<<ncells * nch, kThreads, sm, s>>>(what, wfine, muD, nup, nufp, ws, tb.tw, tb.phip, tb.Ktab, t.J,
+                                                      nch);
+    k_i24_vjp<n, T><<<ncells * nch, kThreads, sm, s>>>(what, wfine, muK2, mu4, nup, nufp, ws, tb.tw, tb.psi, t.J,
+                                                       nch);
     launches += 3;
+    if (nch > 1) {
+      k_add_chunks<T><<<(ncells * 5 * n * n + kThreads * 8 - 1) / (kThreads * 8), kThreads, 0, s>>>(
+          (const T*)nup, (const T*)nufp, (T*)nu, nuf, nch, ncells, (size_t)n * n);
+      ++launches;
+    }
   }
   end();
   const int nunits = ncells * t.J * vw.nmc;
