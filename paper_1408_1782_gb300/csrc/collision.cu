@@ -65,6 +65,12 @@ int i3_variant_bps(int n, int prec, int variant) {
 #undef QBE_CALL
 }
 
+int i3_concurrency(int n, int prec, int variant, int grid, int total) {
+#define QBE_CALL(nn, T) i3_variant_concurrency<nn, T>(variant, grid, total)
+  QBE_SIZE_SWITCH(QBE_CALL, 1)
+#undef QBE_CALL
+}
+
 const char* i3_variant_desc(int n, int prec, int variant) {
 #define QBE_CALL(nn, T) i3_variant_name<nn, T>(variant)
   QBE_SIZE_SWITCH(QBE_CALL, nullptr)

@@ -1000,6 +1000,29 @@ int i3_default_variant() {
   else return 0;
 }
 
+// Work units (or, for the cluster form, clusters) a launch of variant v with `grid` blocks and
+// `total` units processes at once: the persistent grid the launcher uses (see i3_group_n).  Unit u
+// goes to block (cluster) u mod this number.
+template <int n, class T>
+int i3_variant_concurrency(int v, int grid, int total) {
+  if (v < 0 || v >= i3_nvariants<n, T>()) v = 0;
+  int g = total < grid ? total : grid;
+  if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
+    int ncl = grid / kI3Cluster;
+    const int cmax = i3_max_clusters<n>();
+    if (ncl > cmax) ncl = cmax;
+    if (ncl > total) ncl = total;
+    g = ncl < 1 ? 1 : ncl;
+  } else {
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int gmax = nsm * i3_blocks_per_sm<n, T>(v);
+    if (g > gmax) g = gmax;
+  }
+  return g < 1 ? 1 : g;
+}
+
 template <int n, class T>
 const char* i3_variant_name(int v) {
   if (v < 0 || v >= i3_nvariants<n, T>()) return nullptr;

@@ -7,6 +7,7 @@ template cudaError_t collide_batch_n<128, float>(const Tables&, CollisionWork&, 
 template int i3_blocks_per_sm<128, float>(int);
 template int i3_variant_count<128, float>();
 template int i3_default_variant<128, float>();
+template int i3_variant_concurrency<128, float>(int, int, int);
 template const char* i3_variant_name<128, float>(int);
 template cudaError_t collide_vjp_n<128, float>(const Tables&, CollisionWork&, VjpWork&, const double*,
                                               const double* const*, double* const*, int, int, int, cudaStream_t,

@@ -7,6 +7,7 @@ template cudaError_t collide_batch_n<16, double>(const Tables&, CollisionWork&, 
 template int i3_blocks_per_sm<16, double>(int);
 template int i3_variant_count<16, double>();
 template int i3_default_variant<16, double>();
+template int i3_variant_concurrency<16, double>(int, int, int);
 template const char* i3_variant_name<16, double>(int);
 template cudaError_t collide_vjp_n<16, double>(const Tables&, CollisionWork&, VjpWork&, const double*,
                                               const double* const*, double* const*, int, int, int, cudaStream_t,

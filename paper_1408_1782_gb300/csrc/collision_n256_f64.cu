@@ -7,6 +7,7 @@ template cudaError_t collide_batch_n<256, double>(const Tables&, CollisionWork&,
 template int i3_blocks_per_sm<256, double>(int);
 template int i3_variant_count<256, double>();
 template int i3_default_variant<256, double>();
+template int i3_variant_concurrency<256, double>(int, int, int);
 template const char* i3_variant_name<256, double>(int);
 template cudaError_t collide_vjp_n<256, double>(const Tables&, CollisionWork&, VjpWork&, const double*,
                                               const double* const*, double* const*, int, int, int, cudaStream_t,

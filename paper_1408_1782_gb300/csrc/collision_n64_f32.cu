@@ -7,6 +7,7 @@ template cudaError_t collide_batch_n<64, float>(const Tables&, CollisionWork&, c
 template int i3_blocks_per_sm<64, float>(int);
 template int i3_variant_count<64, float>();
 template int i3_default_variant<64, float>();
+template int i3_variant_concurrency<64, float>(int, int, int);
 template const char* i3_variant_name<64, float>(int);
 template cudaError_t collide_vjp_n<64, float>(const Tables&, CollisionWork&, VjpWork&, const double*,
                                               const double* const*, double* const*, int, int, int, cudaStream_t,

@@ -209,12 +209,15 @@ int i3_variant_count();
 template <int n, class T>
 int i3_default_variant();
 template <int n, class T>
+int i3_variant_concurrency(int variant, int grid, int total);
+template <int n, class T>
 const char* i3_variant_name(int variant);
 // Launch variants of the I3 kernel ("tile shapes" the autotuner chooses among) for a grid and
 // precision: their number, resident blocks per SM, and a description.
 int i3_variants(int n, int prec);
 int i3_default(int n, int prec);
 int i3_variant_bps(int n, int prec, int variant);
+int i3_concurrency(int n, int prec, int variant, int grid, int total);
 const char* i3_variant_desc(int n, int prec, int variant);
 // The collision operator in parts (collision_kernels.cuh): the per-cell terms before I3, the I3
 // work queue over one or several simulations of the same padded size, the per-cell assembly.

@@ -1,5 +1,6 @@
 // C ABI (include/qbe.h): solver handle, argument checks, host/device copies
 // and the split time step of Sec. 4.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -849,9 +850,12 @@ namespace {
 // The I3 launch shape of a group of simulations of one padded size and precision (a single
 // simulation is a group of one): for every launch variant, persistent grid (blocks per SM) and
 // m-chunking, two waves of the group's work queue are timed on the simulations' current state
-// (the per-cell terms are computed first, so the I3 inputs are those of the state) and the launch
-// time is extrapolated by waves, ceil(units / grid) x (time per wave).  The fastest shape is set
-// on every member; returns its predicted launch time in ms.
+// (the per-cell terms are computed first, so the I3 inputs are those of the state).  The launch
+// assigns unit u to block (cluster) u mod G, so its time is that of the busiest block: the sample's
+// time divided by its busiest block's m-evaluations gives the cost of one m, and the candidate's
+// time is that cost times the busiest block's m-evaluations over the whole queue (units of
+// different members carry different numbers of m).  The fastest shape is set on every member;
+// returns its predicted launch time in ms.
 int tune_group(const std::vector<qbe_handle*>& hs, cudaStream_t s, double* best_ms, std::string& err) {
   if (hs.empty()) return QBE_ERR_ARG;
   qbe_handle* h0 = hs[0];
@@ -906,9 +910,27 @@ int tune_group(const std::vector<qbe_handle*>& hs, cudaStream_t s, double* best_
       if (grid < 1) grid = 1;
       for (int nmc = nmc_top; nmc >= 1 && rc == QBE_OK; nmc = (nmc == 1 ? 0 : (nmc + 1) / 2)) {
         apply(v, nmc);
-        long long total = 0;
-        for (size_t i = 0; i < hs.size(); ++i) total += (long long)nc[i] * hs[i]->tab.J * hs[i]->cw.nmc;
-        const int sample = (int)(total < 2LL * grid ? total : 2LL * grid);
+        // the queue's units in launch order, each with its number of m evaluations
+        std::vector<int> mwork;
+        for (size_t i = 0; i < hs.size(); ++i) {
+          const CollisionWork& cw = hs[i]->cw;
+          const int M = hs[i]->tab.M;
+          for (long long u = 0; u < (long long)nc[i] * hs[i]->tab.J * cw.nmc; ++u) {
+            const int mc = (int)(u % cw.nmc), m0 = mc * cw.mch;
+            mwork.push_back((M - m0) < cw.mch ? (M - m0) : cw.mch);
+          }
+        }
+        const long long total = (long long)mwork.size();
+        const int conc_full = i3_concurrency(n, prec, v, grid, (int)(total < INT_MAX ? total : INT_MAX));
+        const int sample = (int)(total < 2LL * conc_full ? total : 2LL * conc_full);
+        const int conc_sample = i3_concurrency(n, prec, v, grid, sample);
+        auto busiest = [&](long long units, int conc) {   // m evaluations of the busiest block
+          std::vector<long long> load(conc, 0);
+          for (long long u = 0; u < units; ++u) load[u % conc] += mwork[u];
+          long long mx = 0;
+          for (long long x : load) mx = x > mx ? x : mx;
+          return mx;
+        };
         long long lc = 0;
         cudaError_t e = i3_group(tabs.data(), cws.data(), nc.data(), (int)hs.size(), h0->cw.ws, grid, s, lc, sample);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
@@ -923,12 +945,8 @@ int tune_group(const std::vector<qbe_handle*>& hs, cudaStream_t s, double* best_
           rc = QBE_ERR_CUDA;
           break;
         }
-        // the kernel caps the grid at the variant's residency; waves over the launched blocks
-        int g = grid;
-        const int gres = nsm * i3_variant_bps(n, prec, v);
-        if (g > gres) g = gres;
-        const double per_wave = ms / (double)((sample + g - 1) / g);
-        const double pred = per_wave * (double)((total + g - 1) / g);
+        const double per_m = ms / (double)busiest(sample, conc_sample);
+        const double pred = per_m * (double)busiest(total, conc_full);
         if (pred < best) { best = pred; bv = v; bgrid = grid; bnmc = nmc; }
         if (nmc == 1) break;
       }
