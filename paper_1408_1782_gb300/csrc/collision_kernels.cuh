@@ -505,8 +505,8 @@ template <> struct FusedShapes<64> {
 template <> struct FusedShapes<96> {
   static constexpr int T0 = 768, B0 = 1, M0 = 0, T1 = 768, B1 = 1, M1 = 2, T2 = 384, B2 = 2, M2 = 2, DEFAULT = 3;
 };
-template <> struct FusedShapes<128> {
-  static constexpr int T0 = 512, B0 = 1, M0 = 1, T1 = 1024, B1 = 1, M1 = 2, T2 = 1024, B2 = 1, M2 = 0, DEFAULT = 0;
+template <> struct FusedShapes<128> {   // variant 4: k_i3_wl, 94.9 ms (shape 0: 101.1 ms)
+  static constexpr int T0 = 512, B0 = 1, M0 = 1, T1 = 1024, B1 = 1, M1 = 2, T2 = 1024, B2 = 1, M2 = 0, DEFAULT = 4;
 };
 
 // --------------------------------------------------------------------------
@@ -885,7 +885,7 @@ template <int n, class T>
 constexpr int i3_nvariants() {
   if constexpr (std::is_same<T, float>::value) {
     if constexpr (use_i3_cluster<n>()) return 1;
-    else if constexpr (use_i3_fused<n>()) return 4;
+    else if constexpr (use_i3_fused<n>()) return n == kWlN ? 5 : 4;   // 128 points: + k_i3_wl
     else return 1;
   } else {
     return 4;
@@ -908,6 +908,9 @@ I3Launch i3_variant(int v) {
       l = {(const void*)k_i3_fused<n, S::T1, S::B1, S::M1>, S::T1, i3_fused_smem_bytes<n>(), false, names[S::M1]};
     else if (v == 2)
       l = {(const void*)k_i3_fused<n, S::T2, S::B2, S::M2>, S::T2, i3_fused_smem_bytes<n>(), false, names[S::M2]};
+    else if (v == 4 && n == kWlN)
+      l = {(const void*)k_i3_wl, kWlThreads, i3_wl_smem_bytes(), false,
+           "fused, warp-local passes, register accumulation"};
     else
       l = {(const void*)k_i3_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>(), false, "shared-memory, 1024 threads"};
   } else if constexpr (std::is_same<T, float>::value) {

@@ -278,3 +278,251 @@ __global__ void __launch_bounds__(NT, MINB) k_i3_fused(const I3Jobs<float> jobs,
     __syncthreads();   // psm is reloaded by the next unit
   }
 }
+
+// --------------------------------------------------------------------------
+// The fused FP32 I3 kernel with warp-local passes (padded grid of 128 points, 512 threads, the
+// accumulation of mode 1).  In the row passes warp w owns rows [8 w, 8 w + 8), in the column passes
+// warp pair g owns columns [16 g, 16 g + 16): their stages synchronise with __syncwarp or a named
+// barrier of the pair, and the block synchronises only where the passes change ownership (rows ->
+// columns, columns -> rows), twice per convolution instead of seven times, so warps in different
+// stages overlap their shared-memory, global and arithmetic latencies.  Field layout: element
+// (x, y) at x * WL_PITCH + y + y / 16 (one pad word per 16 elements, row pitch 146 = 2 mod 16),
+// which keeps every stage's accesses free of bank conflicts under the lane mappings below.
+// --------------------------------------------------------------------------
+constexpr int kWlN = 128, kWlThreads = 512, kWlPitch = 146;
+
+__device__ __forceinline__ int wl_addr(int x, int y) { return x * kWlPitch + y + (y >> 4); }
+
+__device__ __forceinline__ void wl_pair_sync(int g) {   // the two warps of pair g (ids 1..8)
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(64) : "memory");
+}
+
+constexpr int kWlPsiPitch = kWlN + 1;   // psi'_j rows padded: the two half-warps of a column stage
+                                         // read rows 16 apart, which would share banks at pitch 128
+constexpr size_t i3_wl_smem_bytes() {    // twiddles (two orders), the skewed field, psi'_j
+  return (size_t)(2 * kWlN + kWlN * kWlPitch) * sizeof(float2) + (size_t)kWlN * kWlPsiPitch * sizeof(float);
+}
+
+// Column pass stages of warp pair g on its 16 columns (tt = thread index within the pair).
+// Stage A: tasks (column c = tt mod 16, t2 = tt / 16 + 4 i); stage B: (c, k1 = tt / 16 + 4 i).
+template <int SIGN>
+__device__ __forceinline__ void wl_cols_stage_a(float2* G, const float2* tw, int g, int tt) {
+  constexpr int A = Split<kWlN>::A, B = Split<kWlN>::B;
+  const int y = 16 * g + (tt & 15);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int t2 = (tt >> 4) + 4 * i;
+    float2 v[A];
+#pragma unroll
+    for (int k = 0; k < A; ++k) v[k] = G[wl_addr(B * k + t2, y)];
+    if (SIGN < 0) {
+      dft<A, -1>(v);
+#pragma unroll
+      for (int k = 1; k < A; ++k) v[k] = cmul(v[k], tw[t2 * A + k]);
+    } else {
+#pragma unroll
+      for (int k = 1; k < A; ++k) v[k] = cmulc(v[k], tw[t2 * A + k]);
+      dft<A, 1>(v);
+    }
+#pragma unroll
+    for (int k = 0; k < A; ++k) G[wl_addr(B * k + t2, y)] = v[k];
+  }
+}
+
+// Row pass stage B of warp w on its 8 rows: tasks (row 8 w + (lane mod 8), k1 = lane / 8 + 4 i).
+template <int SIGN>
+__device__ __forceinline__ void wl_rows_stage_b(float2* G, int w, int lane) {
+  constexpr int B = Split<kWlN>::B;
+  const int x = 8 * w + (lane & 7);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int k1 = (lane >> 3) + 4 * i;
+    float2 b[B];
+#pragma unroll
+    for (int t = 0; t < B; ++t) b[t] = G[wl_addr(x, B * k1 + t)];
+    dft<B, SIGN>(b);
+#pragma unroll
+    for (int t = 0; t < B; ++t) G[wl_addr(x, B * k1 + t)] = b[t];
+  }
+}
+
+__global__ void __launch_bounds__(kWlThreads, 1) k_i3_wl(const I3Jobs<float> jobs, float2* ws,
+                                                        const float2* __restrict__ gtw) {
+  using C2 = float2;
+  constexpr int n = kWlN, A = Split<n>::A, B = Split<n>::B, P = n * n, NT = kWlThreads;
+  constexpr int TPT = n * B / NT;   // 4 row tasks (row, t2) per thread in the fused row stages
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tw = reinterpret_cast<C2*>(smem_raw);                   // tw[t2 A + k1]
+  C2* twT = tw + n;                                           // twT[k1 B + t2]
+  C2* G = twT + n;                                            // skewed field
+  float* psm = reinterpret_cast<float*>(G + n * kWlPitch);    // psi'_j of the current unit, [n][kWlPsiPitch]
+  __shared__ unsigned char xmask[n];
+  for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
+    const int k = freq_of_pos<n>(pos);
+    xmask[pos] = ((k < n / 4) || (k >= n - n / 4)) ? 1 : 0;
+    twT[(pos % A) * B + pos / A] = gtw[pos];
+  }
+  load_twiddles<n>(tw, gtw);
+  C2* Sig = ws + (size_t)blockIdx.x * 3 * P;   // [2][P]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = w >> 1, tt = tid & 63;
+  const int t2r = lane & 15;                   // t2 of this thread's row tasks
+  // row task k of this thread: row 8 w + lane / 16 + 2 k, t2 = lane mod 16
+  auto row_of = [&](int k) { return 8 * w + (lane >> 4) + 2 * k; };
+  for (int gunit = blockIdx.x; gunit < jobs.total; gunit += gridDim.x) {
+    const I3Job<float>& jb = jobs.job[i3_job_of(jobs, gunit)];
+    const int unit = gunit - jb.unit_begin;
+    const int J = jb.J, M = jb.M, nmc = jb.nmc, mch = jb.mch;
+    const C2* what = jb.what;
+    const C2* __restrict__ phase = jb.phase;
+    const int c = unit / (J * nmc);
+    const int j = (unit / nmc) % J;
+    const int mc = unit % nmc;
+    C2* acc = jb.K3part + (size_t)unit * 2 * P;
+    {
+      const float4* src = reinterpret_cast<const float4*>(jb.psip_s + (size_t)j * P);
+      for (int i4 = tid; i4 < P / 4; i4 += NT) {
+        const float4 q = src[i4];
+        float* d = psm + (4 * i4 / n) * kWlPsiPitch + (4 * i4) % n;
+        d[0] = q.x; d[1] = q.y; d[2] = q.z; d[3] = q.w;
+      }
+      __syncthreads();
+    }
+    const C2* wf = jb.wfine + (size_t)c * 2 * P;
+    const int m0 = mc * mch, m1 = min(M, m0 + mch);
+    for (int m = m0; m < m1; ++m) {
+      const C2* px = phase + ((size_t)j * M + m) * 2 * n;
+      const C2* py = px + n;
+      const bool first_m = (m == m0);
+      // shifted pairs: columns (stage B loads the phase-multiplied Xi coefficients), rows (stage A
+      // stores the shifted field)
+      for (int p = 0; p < 2; ++p) {
+        const C2* in = what + ((size_t)c * 4 + p) * P;
+        {
+          const int y = 16 * g + (tt & 15);
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const int k1 = (tt >> 4) + 4 * i;
+            C2 b[B];
+#pragma unroll
+            for (int t = 0; t < B; ++t) {
+              const int x = B * k1 + t;
+              b[t] = (xmask[x] && xmask[y]) ? cmul(in[x * n + y], cmul(px[x], py[y])) : zero2<float>();
+            }
+            dft<B, 1>(b);
+#pragma unroll
+            for (int t = 0; t < B; ++t) G[wl_addr(B * k1 + t, y)] = b[t];
+          }
+        }
+        wl_pair_sync(g);
+        wl_cols_stage_a<1>(G, tw, g, tt);
+        __syncthreads();
+        wl_rows_stage_b<1>(G, w, lane);
+        __syncwarp();
+        C2* S = Sig + (size_t)p * P;
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+          const int x = row_of(k);
+          C2 v[A];
+#pragma unroll
+          for (int k1 = 0; k1 < A; ++k1) v[k1] = G[wl_addr(x, B * k1 + t2r)];
+#pragma unroll
+          for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2r]);
+          dft<A, 1>(v);
+#pragma unroll
+          for (int t1 = 0; t1 < A; ++t1) S[x * n + B * t1 + t2r] = v[t1];
+        }
+        __syncthreads();   // S complete (the row passes below read other warps' rows of it) and G free
+      }
+      for (int p = 0; p < 2; ++p) {
+        const C2* Sp = Sig + (size_t)p * P;      // rewritten every m: plain (coherent) loads
+        C2* accp = acc + (size_t)p * P;
+        C2 racc[TPT][A];
+        for (int a = 0; a < 4; ++a) {
+          const C2* __restrict__ wa = wf + (size_t)(a >> 1) * P;
+          const C2* Sa = Sig + (size_t)(a >> 1) * P;
+          const bool im = (a & 1) != 0;
+          // forward rows of w_a Sigma_p (warp-local): stage A loads the product, stage B
+#pragma unroll
+          for (int k = 0; k < TPT; ++k) {
+            const int x = row_of(k);
+            C2 v[A];
+#pragma unroll
+            for (int t1 = 0; t1 < A; ++t1) {
+              const int idx = x * n + B * t1 + t2r;
+              const C2 z = wa[idx];
+              v[t1] = cscale(Sp[idx], im ? z.y : z.x);
+            }
+            dft<A, -1>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], twT[k1 * B + t2r]);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) G[wl_addr(x, B * k1 + t2r)] = v[k1];
+          }
+          __syncwarp();
+          wl_rows_stage_b<-1>(G, w, lane);
+          __syncthreads();
+          // columns (pair-local): forward stage A, stage B with psi'_j, inverse stage A
+          wl_cols_stage_a<-1>(G, tw, g, tt);
+          wl_pair_sync(g);
+          {
+            const int y = 16 * g + (tt & 15);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              const int k1 = (tt >> 4) + 4 * i;
+              C2 b[B];
+#pragma unroll
+              for (int t = 0; t < B; ++t) b[t] = G[wl_addr(B * k1 + t, y)];
+              dft<B, -1>(b);
+              float sc[B];
+#pragma unroll
+              for (int t = 0; t < B; ++t) sc[t] = psm[(B * k1 + t) * kWlPsiPitch + y];
+              dft_scaled<B, 1>(b, sc);
+#pragma unroll
+              for (int t = 0; t < B; ++t) G[wl_addr(B * k1 + t, y)] = b[t];
+            }
+          }
+          wl_pair_sync(g);
+          wl_cols_stage_a<1>(G, tw, g, tt);
+          __syncthreads();
+          // inverse rows (warp-local): stage B, stage A times eta_a S_a, accumulated over a
+          wl_rows_stage_b<1>(G, w, lane);
+          __syncwarp();
+          const float eta = (a == 0) ? 1.f : -1.f;
+#pragma unroll
+          for (int k = 0; k < TPT; ++k) {
+            const int x = row_of(k);
+            float f[A];
+#pragma unroll
+            for (int t1 = 0; t1 < A; ++t1) {
+              const C2 sv = Sa[x * n + B * t1 + t2r];
+              f[t1] = eta * (im ? sv.y : sv.x);
+            }
+            C2 v[A];
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) v[k1] = G[wl_addr(x, B * k1 + t2r)];
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2r]);
+            dft<A, 1>(v);
+#pragma unroll
+            for (int t1 = 0; t1 < A; ++t1) {
+              if (a == 0) racc[k][t1] = mk2(f[t1] * v[t1].x, f[t1] * v[t1].y);
+              else racc[k][t1] = mk2(fmaT(f[t1], v[t1].x, racc[k][t1].x), fmaT(f[t1], v[t1].y, racc[k][t1].y));
+            }
+          }
+          __syncwarp();   // this warp's rows of G are rewritten by the next a's forward stage A
+        }
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+          const int x = row_of(k);
+#pragma unroll
+          for (int t1 = 0; t1 < A; ++t1) {
+            const int idx = x * n + B * t1 + t2r;
+            accp[idx] = first_m ? racc[k][t1] : cadd(accp[idx], racc[k][t1]);
+          }
+        }
+      }
+      __syncthreads();   // G and Sig are rewritten by the next m's shift transforms
+    }
+    __syncthreads();     // psm is reloaded by the next unit
+  }
+}

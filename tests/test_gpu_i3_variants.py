@@ -58,7 +58,7 @@ def test_fp32_variants_match_fp64(qbe, N, J, M, ncells):
     w = inputs.synthetic_w(N, ncells, seed=50 + N, perturb=0.05)
     ref = _collide_all_variants(qbe, w, N, J, M, 0)[0]
     res = _collide_all_variants(qbe, w, N, J, M, 1)
-    assert len(res) == 4
+    assert len(res) == (5 if N == 64 else 4)
     for v, got in res.items():
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err < TOL_F32, (v, err)
@@ -83,4 +83,32 @@ def test_autotune_keeps_a_valid_fast_shape(qbe, prec):
     assert np.abs(after - before).max() <= tol * np.abs(before).max()
     with pytest.raises(qbe.QbeError):
         s.set_i3_shape(variant=shape["nvariants"])
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_grid_and_m_chunks_change_only_the_summation_order(qbe, prec):
+    """qbe_set_i3_shape: a smaller persistent grid and another m-chunking regroup the per-unit partial
+    sums of I3; C[W] agrees with the default shape to rounding, and out-of-range requests fail."""
+    import torch
+
+    N, Nx, J, M = 32, 5, 8, 8
+    w = torch.from_numpy(inputs.synthetic_w(N, Nx, seed=80, perturb=0.05)).cuda()
+    s = qbe.Solver(N, Nx, J=J, M=M, stream=torch.cuda.current_stream(), precision=prec)
+    ref = s.collide(w).cpu().numpy()
+    base = s.i3_shape()
+    tol = 1e-13 if prec == 0 else 1e-6
+    for grid, m_chunks in ((7, 0), (0, 1), (19, base["m_chunks"])):
+        s.set_i3_shape(grid=grid, m_chunks=m_chunks)
+        sh = s.i3_shape()
+        if grid:
+            assert sh["grid"] == grid
+        if m_chunks:
+            assert sh["m_chunks"] == m_chunks
+        got = s.collide(w).cpu().numpy()
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (grid, m_chunks)
+    with pytest.raises(qbe.QbeError):
+        s.set_i3_shape(m_chunks=base["m_chunks"] + 1)       # more than the partial sums hold
+    with pytest.raises(qbe.QbeError):
+        s.set_i3_shape(grid=-1)
     s.close()
