@@ -13,7 +13,9 @@ Prints one JSON line (rank 0).  Metric: C[W] cell*k-pts/s
 grid: the FP32-split form of the workload (steps/s, C[W] cell*k-pts/s, its
 error against the FP64 GPU form and the stored oracle cells, stated
 tolerances) and the adjoint/forward time ratio of the differentiation
-configuration over a short horizon (--forms-horizon, default 2 split steps).
+configuration over a short horizon (--forms-horizon, default 2 split steps),
+with the forward keeping every intermediate state (full tape) and, beside it,
+with a checkpoint every step recomputed by the reverse sweep.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --mode collide [--cells C]   # time C[W] alone on the first C cells
@@ -498,10 +500,18 @@ def measure_forms(args, wl, W0, s64, fp64_ms_per_step, local):
     s.close()
     awl = workload("adjoint_n64")
     H, every = args.forms_horizon, 1
-    adj = measure_adjoint(awl, local, H, every, steps=2, warmup=1, cpu_baseline=False, clocks=True)
+    adj = measure_adjoint(awl, local, H, every, steps=2, warmup=1, cpu_baseline=False, clocks=True, tape="full")
+    ck = measure_adjoint(awl, local, H, every, steps=2, warmup=1, cpu_baseline=False, clocks=False,
+                         tape="checkpoint")
+    adj["checkpointed"] = {k: ck[k] for k in ("value", "unit", "forward_ms_per_split_step",
+                                               "reverse_ms_per_split_step_both_gradients", "e2e")}
+    adj["checkpointed"]["tape_bytes"] = ck["config"]["tape_bytes"]
     adj["note"] = (f"the differentiation configuration (N=64, Nx=128, periodic, B=(0.3,0,0.4), FP32-split) "
-                   f"over {H} split steps with a checkpoint every step; the per-step ratio does not depend on "
-                   f"the horizon (each segment is recomputed once from its checkpoint)")
+                   f"over {H} split steps; value: the forward keeps every intermediate state (full tape, "
+                   f"{adj['config']['tape_bytes'] / 1e9:.2f} GB here, {tape_bytes(awl, 200, True) / 1e9:.1f} GB "
+                   f"for the 200-step horizon), so the reverse sweep recomputes nothing; 'checkpointed': a "
+                   f"checkpoint every step, each step recomputed once by the reverse sweep.  The per-step "
+                   f"ratios do not depend on the horizon")
     return {"fp32_split": fp32, "adjoint": adj}
 
 
@@ -700,16 +710,28 @@ def run_adjoint(args, local):
     H = args.horizon or wl["checkpoint_every"]
     every = min(wl["checkpoint_every"], H)
     line = measure_adjoint(wl, local, H, every, args.steps, args.warmup,
-                           cpu_baseline=not args.no_cpu_baseline, clocks=True)
+                           cpu_baseline=not args.no_cpu_baseline, clocks=True, tape=args.tape)
     line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "scaling": "weak", "vs_baseline": None,
                  "data": "synthetic (seeded Fermi-Dirac-perturbed W, no dataset)"})
     print(json.dumps(line), flush=True)
     return 0
 
 
-def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clocks=True):
-    """Time `steps` gradients of (P_z, Phi_E) after H split steps of the workload `wl` (checkpoint
-    every `every`); returns the adjoint/forward ratio with its roofline, e2e and kernel times."""
+def tape_bytes(wl, H, full):
+    """Device memory of the forward's tape: every intermediate state of the H steps (full), or one
+    checkpoint segment's, which the reverse sweep recomputes (2 s + 2 states per step, s the transport
+    substeps of a half step, as the library counts them)."""
+    import math
+
+    s = max(1, math.ceil(0.5 * wl["dt"] * wl["L"] * wl["Nx"] - 1e-12))
+    return (H if full else 1) * (2 * s + 2) * wl["Nx"] * 4 * wl["N"] ** 2 * 8
+
+
+def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clocks=True, tape="full"):
+    """Time `steps` gradients of (P_z, Phi_E) after H split steps of the workload `wl`; returns the
+    adjoint/forward ratio with its roofline, e2e and kernel times.  tape="full": the forward keeps every
+    intermediate state (qbe_step_taped) and the reverse sweep recomputes nothing; "checkpoint": a
+    checkpoint every `every` steps, each segment recomputed once by the reverse sweep."""
     import numpy as np
     import torch
 
@@ -733,12 +755,18 @@ def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clock
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
+    def record():
+        if tape == "full":
+            s.step_taped(wl["dt"], H)
+        else:
+            s.step_checkpointed(wl["dt"], H, every)
+
     def gradient(events=None):
         s.set_state(W0)
         s.set_bfield(B)
         if events:
             events[0].record(stream)
-        s.step_checkpointed(wl["dt"], H, every)
+        record()
         s.observables(None, out=obs)
         if events:
             events[1].record(stream)
@@ -789,7 +817,7 @@ def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clock
     t0 = time.perf_counter()
     s.set_state(hW)
     s.set_bfield(hB)
-    s.step_checkpointed(wl["dt"], H, every)
+    record()
     obs_host = s.observables()            # D2H of the observables (synchronises)
     t1 = time.perf_counter()
     s.observables_vjp(np.array([1.0, 0.0]), out=hl)
@@ -797,9 +825,12 @@ def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clock
     t2 = time.perf_counter()
     cpu = adjoint_cpu_baseline(wl) if cpu_baseline else None
     conf = config_dict(wl, 1)
-    conf.update({"horizon_steps": H, "checkpoint_every": every,
+    how = ("full tape: every intermediate state kept" if tape == "full"
+           else f"checkpoint every {every}, segments recomputed")
+    conf.update({"horizon_steps": H, "tape": tape, "checkpoint_every": every if tape != "full" else None,
+                 "tape_bytes": tape_bytes(wl, H, tape == "full"),
                  "workload": conf["workload"] + f"; gradient of P_z and Phi_E after {H} split steps "
-                                                f"(checkpoint every {every}) w.r.t. W_0 and B"})
+                                                f"({how}) w.r.t. W_0 and B"})
     line = {
         "metric": "adjoint/forward time ratio", "value": ratio,
         "unit": "reverse s per observable gradient (P_z and Phi_E in one sweep) / forward sweep s",
@@ -918,6 +949,9 @@ def main():
                     default="plain_fp64_n64")
     ap.add_argument("--horizon", type=int, default=0,
                     help="adjoint_n64: split steps per gradient (default: one checkpoint segment, 20)")
+    ap.add_argument("--tape", choices=["full", "checkpoint"], default="full",
+                    help="adjoint_n64: keep every intermediate state of the forward (full) or recompute "
+                         "each checkpoint segment in the reverse sweep (checkpoint)")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None)
     ap.add_argument("--cells", type=int, default=0)
     ap.add_argument("--i3-variant", type=int, default=-1,

@@ -182,12 +182,26 @@ int qbe_collide_vjp_n(qbe_handle* h, int ncot, const double* w, const double* la
  * Errors: QBE_ERR_ARG (nsteps < 1, checkpoint_every < 1), QBE_ERR_STATE. */
 int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_every);
 
+/* qbe_step(h, dt, nsteps) that records a full tape: every intermediate state
+ * of every step (nsteps (2 s + 2) states of device memory, s the transport
+ * substeps of a half step: the inputs of the transport substeps, U and W1 of
+ * the Heun step), so that qbe_step_vjp(_n) recomputes nothing and its
+ * reverse sweep does only the transposed work.  The storage is kept by h
+ * until it is destroyed or a later qbe_step_checkpointed releases it.  The
+ * tape is invalidated as qbe_step_checkpointed's is.  Errors: QBE_ERR_ARG
+ * (nsteps < 1, dt not finite), QBE_ERR_STATE, QBE_ERR_ALLOC (the tape does
+ * not fit: nothing was stepped, the state is unchanged and no tape is
+ * valid), QBE_ERR_CUDA. */
+int qbe_step_taped(qbe_handle* h, double dt, int nsteps);
+
 /* Reverse sweep over the tape of the last qbe_step_checkpointed(h, dt,
- * nsteps, k) call, which mapped W_0 to W_n: lam_init = (dW_n/dW_0)^T
- * lam_final ([Nx][4][N][N]) and, if grad_B is not NULL, grad_B =
- * (dW_n/dB)^T lam_final ([Nx][3]).  Each segment of k steps is recomputed from
- * its checkpoint with every intermediate state kept (k (2 s + 2) states, s
- * the transport substeps of a half step), then swept backwards.  The state
+ * nsteps, k) or qbe_step_taped(h, dt, nsteps) call, which mapped W_0 to W_n:
+ * lam_init = (dW_n/dW_0)^T lam_final ([Nx][4][N][N]) and, if grad_B is not
+ * NULL, grad_B = (dW_n/dB)^T lam_final ([Nx][3]).  With checkpoints, each
+ * segment of k steps is recomputed from its checkpoint with every
+ * intermediate state kept (k (2 s + 2) states, s the transport substeps of a
+ * half step), then swept backwards; a full tape is swept as it is.  Both
+ * tapes give the same result bit for bit.  The state
  * is W_n again on return.  Errors: QBE_ERR_STATE (no valid tape),
  * QBE_ERR_ARG, QBE_ERR_ALLOC, QBE_ERR_CUDA. */
 int qbe_step_vjp(qbe_handle* h, const double* lam_final, double* lam_init, double* grad_B, int on_device);

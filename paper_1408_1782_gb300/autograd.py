@@ -33,14 +33,21 @@ class CollideFn(torch.autograd.Function):
         return None, ctx.solver.collide_vjp(w, _contig(gc))
 
 
+def _record(solver, dt, nsteps, checkpoint_every):
+    """checkpoint_every = 0: keep every intermediate state (no recomputation in the backward)."""
+    if checkpoint_every == 0:
+        return solver.step_taped(dt, nsteps)
+    return solver.step_checkpointed(dt, nsteps, checkpoint_every)
+
+
 class EvolveFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, solver, W0, B, dt, nsteps, checkpoint_every):
         W0, B = _contig(W0), _contig(B)
         solver.set_state(W0)
         solver.set_bfield(B)
-        ctx.gen = solver.step_checkpointed(dt, nsteps, checkpoint_every)
         ctx.solver, ctx.args = solver, (float(dt), int(nsteps), int(checkpoint_every))
+        ctx.gen = _record(solver, *ctx.args)
         ctx.save_for_backward(W0, B)
         Wn = torch.empty_like(W0)
         solver.get_state(Wn)
@@ -54,7 +61,7 @@ class EvolveFn(torch.autograd.Function):
             # the solver ran something else since this forward: record the tape again
             solver.set_state(W0)
             solver.set_bfield(B)
-            ctx.gen = solver.step_checkpointed(*ctx.args)
+            ctx.gen = _record(solver, *ctx.args)
         lam0, gB = solver.step_vjp(_contig(gWn))
         return None, lam0, gB, None, None, None
 
@@ -77,7 +84,11 @@ def collide(solver: "_q.Solver", w: torch.Tensor) -> torch.Tensor:
 
 def evolve(solver: "_q.Solver", W0: torch.Tensor, B: torch.Tensor, dt: float, nsteps: int,
            checkpoint_every: int = 20) -> torch.Tensor:
-    """W_n after nsteps split steps from W0 with field B, differentiable in W0 and B."""
+    """W_n after nsteps split steps from W0 with field B, differentiable in W0 and B.  The backward
+    recomputes each segment of checkpoint_every steps from its checkpoint; checkpoint_every = 0
+    keeps every intermediate state of the forward instead (more device memory, no recomputation)."""
+    if checkpoint_every < 0:
+        raise ValueError("checkpoint_every must be >= 0")
     return EvolveFn.apply(solver, W0, B, dt, nsteps, checkpoint_every)
 
 

@@ -2,6 +2,7 @@
 // and the split time step of Sec. 4.
 #include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -63,8 +64,9 @@ struct qbe_handle {
   bool tape_valid = false;
   double tape_dt = 0.0;
   int tape_nsteps = 0, tape_every = 1;
+  bool tape_full = false;      // snaps holds every step's intermediate states (qbe_step_taped)
   DevBuf ckpt;                 // [ceil(nsteps/every)] states
-  DevBuf snaps;                // [every][2 sA + 2] states of one segment
+  DevBuf snaps;                // [every][2 sA + 2] states of one segment, or [nsteps][2 sA + 2]
   DevBuf adj;                  // [5] states: two cotangent buffers, G1, lF0, final state
   DevBuf small;                // gsum[2], gbar[2], obs_out[2], gB[Nx][3], obs_part[Nx][2]
   DevBuf gradb;                // [ncot][Nx][3] field gradients of a reverse sweep
@@ -606,6 +608,8 @@ int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_e
     return fail(h, QBE_ERR_ARG, "bad dt, nsteps or checkpoint_every");
   DeviceGuard dg(h->g.device);
   h->tape_valid = false;
+  if (h->tape_full) h->snaps.release();   // a full tape's storage; the reverse sweep takes one segment's
+  h->tape_full = false;
   const size_t S = state_elems(h);
   const int every = checkpoint_every < nsteps ? checkpoint_every : nsteps;
   const size_t nck = (size_t)(nsteps + every - 1) / every;
@@ -621,9 +625,35 @@ int qbe_step_checkpointed(qbe_handle* h, double dt, int nsteps, int checkpoint_e
     if (r) return r;
   }
   h->tape_valid = true;
+  h->tape_full = false;
   h->tape_dt = dt;
   h->tape_nsteps = nsteps;
   h->tape_every = every;
+  return QBE_OK;
+}
+
+int qbe_step_taped(qbe_handle* h, double dt, int nsteps) {
+  if (!h) return QBE_ERR_ARG;
+  if (!h->has_state) return fail(h, QBE_ERR_STATE, "no state set");
+  if (!std::isfinite(dt) || nsteps < 1) return fail(h, QBE_ERR_ARG, "bad dt or nsteps");
+  DeviceGuard dg(h->g.device);
+  h->tape_valid = false;
+  const size_t per_step = (size_t)(2 * half_substeps(h, dt) + 2) * state_elems(h);
+  if ((size_t)nsteps > SIZE_MAX / sizeof(double) / per_step) return fail(h, QBE_ERR_ALLOC, "tape size overflows");
+  cudaError_t e = h->snaps.ensure((size_t)nsteps * per_step);
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // an out-of-memory cudaMalloc leaves no sticky error; clear the last-error slot
+    return fail(h, QBE_ERR_ALLOC, std::string("tape storage: ") + cudaGetErrorString(e));
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    const int r = do_step(h, dt, h->snaps.p + (size_t)s * per_step);
+    if (r) return r;
+  }
+  h->tape_valid = true;
+  h->tape_full = true;
+  h->tape_dt = dt;
+  h->tape_nsteps = nsteps;
+  h->tape_every = nsteps;
   return QBE_OK;
 }
 
@@ -646,7 +676,7 @@ int qbe_step_vjp_n(qbe_handle* h, int ncot, const double* lam_final, double* lam
   const int kg = ncot < kmax ? ncot : kmax;
   int r = ensure_vjp(h, kg);
   if (r) return r;
-  if (h->snaps.ensure((size_t)every * per_step) != cudaSuccess ||
+  if ((!h->tape_full && h->snaps.ensure((size_t)every * per_step) != cudaSuccess) ||
       h->adj.ensure((2 * (size_t)ncot + 2 * (size_t)kg + 1) * S) != cudaSuccess ||
       h->small.ensure(small_elems(h)) != cudaSuccess || h->gradb.ensure((size_t)ncot * nb3) != cudaSuccess)
     return fail(h, QBE_ERR_ALLOC, "adjoint sweep storage");
@@ -678,11 +708,14 @@ int qbe_step_vjp_n(qbe_handle* h, int ncot, const double* lam_final, double* lam
     const int s0 = seg * every;
     const int len = (nsteps - s0) < every ? (nsteps - s0) : every;
     // recompute the segment from its checkpoint once, recording every step's intermediate states
-    e = cudaMemcpyAsync(h->W, h->ckpt.p + (size_t)seg * S, sb, cudaMemcpyDeviceToDevice, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "restore checkpoint");
-    for (int i = 0; i < len; ++i) {
-      r = do_step(h, dt, h->snaps.p + (size_t)i * per_step);
-      if (r) return r;
+    // (a full tape already holds them: one segment of nsteps steps)
+    if (!h->tape_full) {
+      e = cudaMemcpyAsync(h->W, h->ckpt.p + (size_t)seg * S, sb, cudaMemcpyDeviceToDevice, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "restore checkpoint");
+      for (int i = 0; i < len; ++i) {
+        r = do_step(h, dt, h->snaps.p + (size_t)i * per_step);
+        if (r) return r;
+      }
     }
     for (int i = len - 1; i >= 0; --i)
       for (int k0 = 0; k0 < ncot; k0 += kg) {

@@ -77,6 +77,7 @@ SIGNATURES = {
     "qbe_collide_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int, _c_int]),
     "qbe_collide_vjp_n": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_int, _c_int]),
     "qbe_step_checkpointed": (_c_int, [_c_void_p, _c_double, _c_int, _c_int]),
+    "qbe_step_taped": (_c_int, [_c_void_p, _c_double, _c_int]),
     "qbe_step_vjp": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_step_vjp_n": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_int]),
     "qbe_observables": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int]),
@@ -365,8 +366,15 @@ class Solver:
                     "qbe_step_checkpointed")
         return self._gen
 
+    def step_taped(self, dt, nsteps):
+        """step(dt, nsteps) keeping every intermediate state, so that step_vjp recomputes nothing
+        (nsteps x (2 s + 2) states of device memory; QbeError if they do not fit)."""
+        self._gen += 1
+        self._check(lib().qbe_step_taped(self._h, float(dt), int(nsteps)), "qbe_step_taped")
+        return self._gen
+
     def step_vjp(self, lam_final, out=None, grad_B=None):
-        """(lam_init, grad_B) for the tape of the last step_checkpointed call."""
+        """(lam_init, grad_B) for the tape of the last step_checkpointed or step_taped call."""
         pl, dev, k1 = _arg(lam_final, self.state_shape)
         out = self._like(lam_final, self.state_shape, out)
         grad_B = self._like(lam_final, (self.Nx, 3), grad_B)

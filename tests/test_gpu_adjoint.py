@@ -250,6 +250,43 @@ def test_step_vjp_segment_length_does_not_matter(qbe):
         assert np.array_equal(l0, out[0][0]) and np.array_equal(gb, out[0][1])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_tape_equals_checkpointed_tape(qbe, precision):
+    """qbe_step_taped keeps every intermediate state of the forward; its reverse sweep (no
+    recomputation) equals the checkpointed sweep bit for bit, for one and for several cotangents,
+    and the forward itself equals plain stepping."""
+    N, Nx, J, M = 16, 4, 4, 3
+    W = inputs.synthetic_w(N, Nx, seed=62, perturb=0.05)
+    B = inputs.uniform_b(Nx, (0.1, 0.2, 0.3))
+    lams = np.stack([inputs.random_field(W.shape, seed=63 + k) for k in range(2)])
+    dt, nsteps = 0.01, 4
+    s = gpu_solver(qbe, N, Nx, J, M, "maxwell", precision=precision, R=2.0)
+    s.set_state(W)
+    s.set_bfield(B)
+    s.step(dt, nsteps)
+    Wn = s.get_state()
+    s.set_state(W)
+    s.step_checkpointed(dt, nsteps, 3)
+    ref = [s.step_vjp(lams[k].copy()) for k in range(2)]
+    ref_many = s.step_vjp_many(lams)
+    s.set_state(W)
+    s.step_taped(dt, nsteps)
+    assert np.array_equal(s.get_state(), Wn)
+    got = [s.step_vjp(lams[k].copy()) for k in range(2)]
+    got_many = s.step_vjp_many(lams)
+    assert np.array_equal(s.get_state(), Wn)
+    for k in range(2):
+        assert np.array_equal(got[k][0], ref[k][0]) and np.array_equal(got[k][1], ref[k][1]), k
+    assert np.array_equal(got_many[0], ref_many[0]) and np.array_equal(got_many[1], ref_many[1])
+    s.step_checkpointed(dt, 2, 1)       # a checkpointed forward after a full tape sweeps its own tape
+    a = s.step_vjp(lams[0].copy())
+    s.set_state(Wn)
+    s.step_checkpointed(dt, 2, 2)
+    b = s.step_vjp(lams[0].copy())
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    s.close()
+
+
 def observables_grad(s, W, B, dt, nsteps, every):
     s.set_state(W)
     s.set_bfield(B)
@@ -364,6 +401,11 @@ def test_autograd_functions(qbe):
     ref = s.collide_vjp(W[:2].copy(), lam.cpu().numpy())
     assert np.abs(w.grad.cpu().numpy() - ref).max() <= 1e-14 * np.abs(ref).max()
     del other
+    # checkpoint_every = 0: the full tape, the same gradients
+    W1 = torch.from_numpy(W).cuda().requires_grad_(True)
+    B1 = torch.from_numpy(B).cuda().requires_grad_(True)
+    A.observables(s, A.evolve(s, W1, B1, dt, nsteps, 0))[0].backward()
+    assert torch.equal(W1.grad, W0.grad) and torch.equal(B1.grad, B0.grad)
     s.close()
 
 
