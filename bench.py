@@ -896,6 +896,7 @@ def run_vjp_only(args, wl, local):
     W = inputs.synthetic_w(N, wl["Nx"], L=wl["L"], seed=0, perturb=wl["perturb"])[:cells]
     w = torch.from_numpy(W.copy()).cuda()
     K = max(1, args.cotangents)
+    s.set_vjp_i3_variant(args.vjp_i3_variant)
     lam = torch.from_numpy(np.stack([inputs.random_field(W.shape, seed=1 + k) for k in range(K)])).cuda()
     g = torch.empty_like(lam)
 
@@ -925,6 +926,7 @@ def run_vjp_only(args, wl, local):
             "unit": "cell·k-pts/s", "cells": cells, "cotangents": K, "steps": args.steps, "warmup": args.warmup,
             "ms_per_product": t_ms / args.steps / K, "vjp_i3_ms_per_launch": v_ms / max(v_n, 1),
             "cotangents_per_launch": kgrp, "vjp_i3_tflops": flops / (v_ms / max(v_n, 1) * 1e-3) / 1e12,
+            "vjp_i3_variant": s.vjp_i3_variant()[0],
             "dtype": "f64" if wl.get("precision", 0) == 0 else "f32-split", "workload": wl["name"]}
     print(json.dumps(line), flush=True)
     s.close()
@@ -957,6 +959,8 @@ def main():
     ap.add_argument("--i3-variant", type=int, default=-1,
                     help="--mode collide: I3 launch variant (qbe_set_i3_shape); default: the library's")
     ap.add_argument("--autotune", action="store_true", help="--mode collide: run qbe_autotune first")
+    ap.add_argument("--vjp-i3-variant", type=int, default=-1,
+                    help="--mode vjp: I3 transpose kernel variant (qbe_set_vjp_i3_variant); default: the library's")
     ap.add_argument("--compare-untuned", action="store_true",
                     help="batched workloads: also time the steps with the default launch shapes first")
     ap.add_argument("--cotangents", type=int, default=1,

@@ -313,8 +313,9 @@ int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launc
  *     64 KB shared-memory chunks (3 blocks per SM) or 128 threads and 32 KB
  *     chunks (6 per SM), or the staged kernel with its global loads and
  *     stores fused into the line stages (256 threads, 64 KB).  FP32-split form, 2N = 64, 96, 128: the fused
- *     shared-memory kernel in two thread/accumulation shapes, or the kernel
- *     whose element passes go through shared memory; 2N <= 32: the latter
+ *     shared-memory kernel in three thread/accumulation shapes, or the kernel
+ *     whose element passes go through shared memory, and at 2N = 128 also the
+ *     kernel with warp-local passes; 2N <= 32: the element-pass kernel
  *     only; 2N = 192, 256: the cluster kernel only;
  *   - the persistent grid (blocks; at most the variant's residency);
  *   - the number of m-chunks per (cell, angle) work unit.
@@ -325,8 +326,8 @@ int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launc
  * exceed the value set when the handle was created (QBE_ERR_ARG).
  * qbe_autotune times every variant x grid x m-chunking candidate on the
  * current state -- two waves of the I3 work queue each, after the per-cell
- * terms of that state, extrapolated by the number of waves -- and keeps the
- * fastest; best_ms (may be NULL) receives its predicted I3 launch time.  It
+ * terms of that state, scaled from the sample's busiest block to the busiest
+ * block of the whole queue -- and keeps the fastest; best_ms (may be NULL) receives its predicted I3 launch time.  It
  * needs a state (QBE_ERR_STATE), synchronises the stream, and leaves the state
  * unchanged.  The variants compute the same sums in different orders:
  * results of different shapes agree to rounding (FP64: ~1e-15 relative; the
@@ -335,6 +336,18 @@ int qbe_i3_shape(const qbe_handle* h, int* variant, int* nvariants, int* grid, i
 const char* qbe_i3_variant_name(const qbe_handle* h, int variant);
 int qbe_set_i3_shape(qbe_handle* h, int variant, int grid, int m_chunks);
 int qbe_autotune(qbe_handle* h, double* best_ms);
+
+/* Kernel variant of the transpose of the I3 term in the collision product
+ * (qbe_collide_vjp, and the reverse sweeps of qbe_step_vjp).  FP32-split form
+ * at 2N = 128: variant 0 (the default) runs the convolutions on warp-local
+ * passes with the sums into XZ held in registers (one cotangent per product),
+ * variant 1 the kernel whose element passes go through shared memory; every
+ * other grid and precision has one variant.  The variants agree to rounding.
+ * qbe_vjp_i3_variant reports the current variant and the count (either
+ * pointer may be NULL); qbe_set_vjp_i3_variant sets it (-1: the default;
+ * QBE_ERR_ARG when out of range). */
+int qbe_vjp_i3_variant(const qbe_handle* h, int* variant, int* nvariants);
+int qbe_set_vjp_i3_variant(qbe_handle* h, int variant);
 
 /* ------------------------------------------------------------------------
  * Batches of independent simulations: several solver handles -- any mix of

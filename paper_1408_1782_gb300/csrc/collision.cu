@@ -242,6 +242,8 @@ cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const d
 // -> 68 %), so it takes one cotangent at a time.
 int vjp_cotangent_group(const Tables& t, int prec) { return (prec == 1 && t.n <= 128) ? 1 : kMaxCotangents; }
 
+int vjp_i3_variants(int n, int prec) { return (prec == 1 && n == 128) ? 2 : 1; }
+
 cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec, int kcap) {
   const size_t P = (size_t)t.n * t.n;
   int dev = 0, nsm = 0;

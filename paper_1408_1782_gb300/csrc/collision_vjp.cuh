@@ -708,6 +708,8 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
   }
 }
 
+#include "i3_vjp_wl.cuh"
+
 // --------------------------------------------------------------------------
 // Final: nu = direct + I1 + I2/I4 + 2 nu_f (into w0) + sum of the I3 real
 // partials; gradient = 4 E P (nu + IFFT(H) / n^2) with H the sum of the I3
@@ -804,6 +806,15 @@ void set_vjp_smem_attributes() {
   cudaFuncSetAttribute(k_vjp_final<n, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     cudaFuncSetAttribute(k_i3_vjp_smem<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_smem_bytes<n>());
+  if constexpr (std::is_same<T, float>::value && n == kWlN)
+    cudaFuncSetAttribute(k_i3_vjp_wl<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)i3_vjp_wl_smem_bytes());
+}
+
+// I3 transpose kernels per (n, T): the warp-local kernel (FP32, 128 points, one cotangent) is variant
+// 0 where it exists, the element-pass shared-memory kernel variant 1; other sizes have one.
+template <int n, class T>
+constexpr int i3_vjp_variant_count() {
+  return (std::is_same<T, float>::value && n == kWlN) ? 2 : 1;
 }
 
 // Forward prep/I1/I2+I4 once (the VJP needs wfine, D^, K2, K4^), then per cotangent the seed and the
@@ -869,11 +880,20 @@ cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const
   const int nunits = ncells * t.J * vw.nmc;
   const int grid = nunits < vw.grid ? nunits : vw.grid;
   begin(KG_VJP_I3);
-  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
-    k_i3_vjp_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(
-        what, wfine, (C2*)vw.mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M, vw.nmc,
-        vw.mch, nunits, K, c_stride, part_stride, spart_stride);
-  else
+  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>()) {
+    bool wl = false;
+    if constexpr (n == kWlN) {
+      wl = (K == 1 && vw.i3v == 0);
+      if (wl)
+        k_i3_vjp_wl<n><<<grid, kWlThreads, i3_vjp_wl_smem_bytes(), s>>>(
+            what, wfine, (C2*)vw.mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M,
+            vw.nmc, vw.mch, nunits);
+    }
+    if (!wl)
+      k_i3_vjp_smem<n><<<grid, kThreadsI3Smem, i3_smem_bytes<n>(), s>>>(
+          what, wfine, (C2*)vw.mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw, tb.psip_s, tb.phase, t.J, t.M,
+          vw.nmc, vw.mch, nunits, K, c_stride, part_stride, spart_stride);
+  } else
     k_i3_vjp<n, T><<<grid, kThreads, sm, s>>>(what, wfine, (C2*)vw.mu3, (C2*)vw.part_r, (C2*)vw.part_s, ws, tb.tw,
                                               tb.psip_s, tb.phase, t.J, t.M, vw.nmc, vw.mch, nunits, K, c_stride,
                                               part_stride, spart_stride);
@@ -894,7 +914,12 @@ template <int n, class T>
 int i3_vjp_blocks_per_sm() {
   set_vjp_smem_attributes<n, T>();
   int b = 0;
-  if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
+  if constexpr (std::is_same<T, float>::value && n == kWlN) {
+    int b2 = 0;   // the grid serves both variants: the smaller residency of the two
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_vjp_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_i3_vjp_wl<n>, kWlThreads, i3_vjp_wl_smem_bytes());
+    if (b2 < b) b = b2;
+  } else if constexpr (std::is_same<T, float>::value && use_i3_smem<n>())
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_vjp_smem<n>, kThreadsI3Smem, i3_smem_bytes<n>());
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_i3_vjp<n, T>, kThreads, smem_bytes<n, T>());

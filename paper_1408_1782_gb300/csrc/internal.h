@@ -112,6 +112,7 @@ struct VjpWork {
   int nmc = 1;           // m-chunks per (cell, j) unit of the I3 transpose kernel
   int mch = 1;
   int grid = 0;          // persistent grid of the I3 transpose kernel
+  int i3v = 0;           // I3 transpose kernel variant (vjp_i3_variants)
   void* nu = nullptr;    // [nb][2][n*n] fine-grid cotangent pairs (0,1), (2,3)
   void* nuf = nullptr;   // [nb][n*n] (real) cotangent of f = 2 w0 - 1
   void* muD = nullptr;   // [nb][2][n*n] cotangent of D pairs (1,2), (3,-)
@@ -249,6 +250,8 @@ cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const d
 cudaError_t alloc_vjp_work(const Tables& t, int nb, VjpWork& vw, int prec = 0, int kcap = 1);
 // How many cotangents one product should carry for this grid and precision form (1 .. kMaxCotangents).
 int vjp_cotangent_group(const Tables& t, int prec);
+// I3 transpose kernel variants for a padded grid and precision (0: the default, the fastest measured).
+int vjp_i3_variants(int n, int prec);
 void free_vjp_work(VjpWork& vw);
 template <int n, class T>
 cudaError_t collide_vjp_n(const Tables& t, CollisionWork& cw, VjpWork& vw, const double* w, const double* const* lam,

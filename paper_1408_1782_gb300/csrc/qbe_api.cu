@@ -64,7 +64,8 @@ struct qbe_handle {
   bool tape_valid = false;
   double tape_dt = 0.0;
   int tape_nsteps = 0, tape_every = 1;
-  bool tape_full = false;      // snaps holds every step's intermediate states (qbe_step_taped)
+  bool tape_full = false;
+  int vjp_i3v = 0;             // I3 transpose kernel variant (qbe_set_vjp_i3_variant)      // snaps holds every step's intermediate states (qbe_step_taped)
   DevBuf ckpt;                 // [ceil(nsteps/every)] states
   DevBuf snaps;                // [every][2 sA + 2] states of one segment, or [nsteps][2 sA + 2]
   DevBuf adj;                  // [5] states: two cotangent buffers, G1, lF0, final state
@@ -190,6 +191,7 @@ int ensure_vjp(qbe_handle* h, int kneed = 1) {
     h->lbuf = nullptr;
     return fail(h, QBE_ERR_ALLOC, std::string("adjoint workspace: ") + cudaGetErrorString(e));
   }
+  h->vw.i3v = h->vjp_i3v;
   h->vw_ready = true;
   return QBE_OK;
 }
@@ -385,6 +387,22 @@ int qbe_set_i3_shape(qbe_handle* h, int variant, int grid, int m_chunks) {
     h->cw.mch = (h->tab.M + m_chunks - 1) / m_chunks;
     h->cw.nmc = (h->tab.M + h->cw.mch - 1) / h->cw.mch;
   }
+  return QBE_OK;
+}
+
+int qbe_vjp_i3_variant(const qbe_handle* h, int* variant, int* nvariants) {
+  if (!h) return QBE_ERR_ARG;
+  if (variant) *variant = h->vjp_i3v;
+  if (nvariants) *nvariants = vjp_i3_variants(h->tab.n, h->g.precision);
+  return QBE_OK;
+}
+
+int qbe_set_vjp_i3_variant(qbe_handle* h, int variant) {
+  if (!h) return QBE_ERR_ARG;
+  const int nv = vjp_i3_variants(h->tab.n, h->g.precision);
+  if (variant < -1 || variant >= nv) return fail(h, QBE_ERR_ARG, "set_vjp_i3_variant: variant out of range");
+  h->vjp_i3v = variant < 0 ? 0 : variant;
+  h->vw.i3v = h->vjp_i3v;
   return QBE_OK;
 }
 

@@ -93,6 +93,8 @@ SIGNATURES = {
     "qbe_i3_variant_name": (ctypes.c_char_p, [_c_void_p, _c_int]),
     "qbe_set_i3_shape": (_c_int, [_c_void_p, _c_int, _c_int, _c_int]),
     "qbe_autotune": (_c_int, [_c_void_p, ctypes.POINTER(_c_double)]),
+    "qbe_vjp_i3_variant": (_c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "qbe_set_vjp_i3_variant": (_c_int, [_c_void_p, _c_int]),
     "qbe_batch_create": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, ctypes.POINTER(_c_void_p)]),
     "qbe_batch_destroy": (None, [_c_void_p]),
     "qbe_batch_last_error": (ctypes.c_char_p, [_c_void_p]),
@@ -493,6 +495,15 @@ class Solver:
         ms = _c_double()
         self._check(lib().qbe_autotune(self._h, ctypes.byref(ms)), "qbe_autotune")
         return ms.value
+
+    def vjp_i3_variant(self):
+        """(variant, count) of the I3 transpose kernel of the collision product."""
+        v, nv = _c_int(), _c_int()
+        self._check(lib().qbe_vjp_i3_variant(self._h, ctypes.byref(v), ctypes.byref(nv)), "qbe_vjp_i3_variant")
+        return v.value, nv.value
+
+    def set_vjp_i3_variant(self, variant=-1):
+        self._check(lib().qbe_set_vjp_i3_variant(self._h, int(variant)), "qbe_set_vjp_i3_variant")
 
 
 def fd_fit_moments(rho4, mom, energy) -> QbeFermiDirac:

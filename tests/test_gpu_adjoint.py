@@ -126,6 +126,38 @@ def test_collide_vjp_fp32_split_matches_fp64_n64(qbe):
     assert err < 5e-6, err
 
 
+@pytest.mark.parametrize("ncells,J,M", [(3, 8, 6), (20, 8, 7)])
+def test_collide_vjp_i3_variants_agree(qbe, ncells, J, M):
+    """FP32-split, N = 64: the warp-local I3 transpose (variant 0, the default) and the element-pass
+    kernel (variant 1) against the FP64 product.  (3, 8, 6): one m per work unit; (20, 8, 7): m-chunks
+    of two with a ragged last chunk, so the partials accumulate over m inside a unit."""
+    import torch
+
+    N = 64
+    W = inputs.synthetic_w(N, ncells, seed=33, perturb=0.05)
+    lam = inputs.random_field(W.shape, seed=34)
+    g64 = vjp(qbe, W, lam, N, J, M, 0)
+    s = qbe.Solver(N, ncells, J=J, M=M, precision=1)
+    assert s.vjp_i3_variant() == (0, 2)
+    w, l = torch.from_numpy(W).cuda(), torch.from_numpy(lam).cuda()
+    out = []
+    for v in (0, 1):
+        s.set_vjp_i3_variant(v)
+        assert s.vjp_i3_variant()[0] == v
+        out.append(s.collide_vjp(w, l).cpu().numpy())
+        err = np.abs(out[-1] - g64).max() / np.abs(g64).max()
+        assert err < 5e-6, (v, err)
+    with pytest.raises(qbe.QbeError):
+        s.set_vjp_i3_variant(2)
+    s.set_vjp_i3_variant(-1)
+    assert s.vjp_i3_variant()[0] == 0
+    assert np.array_equal(s.collide_vjp(w, l).cpu().numpy(), out[0])
+    s.close()
+    s64 = qbe.Solver(N, 1, J=4, M=2, precision=0)
+    assert s64.vjp_i3_variant() == (0, 1)
+    s64.close()
+
+
 def test_collide_vjp_fp32_split_matches_fp64_largest_grid(qbe):
     """N = 128 (the staged FP32 transpose on the 256-point grid), two cotangents in one product
     against the FP64 form's single products."""
