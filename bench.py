@@ -254,6 +254,9 @@ def run_ours(args):
     if args.workload == "adjoint_n64":
         return run_adjoint(args, local)
     wl = workload(args.workload, args.precision)
+    if args.velocity_n and args.mode in ("collide", "vjp"):
+        wl["N"] = args.velocity_n
+        wl["name"] += f" at N={args.velocity_n}"
     if args.mode == "collide":
         return run_collide_only(args, wl, local)
     if args.mode == "vjp":
@@ -956,6 +959,8 @@ def main():
                          "each checkpoint segment in the reverse sweep (checkpoint)")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None)
     ap.add_argument("--cells", type=int, default=0)
+    ap.add_argument("--velocity-n", type=int, default=0,
+                    help="--mode collide / vjp: velocity grid N instead of the workload's (other padded sizes)")
     ap.add_argument("--i3-variant", type=int, default=-1,
                     help="--mode collide: I3 launch variant (qbe_set_i3_shape); default: the library's")
     ap.add_argument("--autotune", action="store_true", help="--mode collide: run qbe_autotune first")

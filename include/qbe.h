@@ -316,7 +316,8 @@ int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launc
  *     shared-memory kernel in three thread/accumulation shapes, or the kernel
  *     whose element passes go through shared memory, and at 2N = 128 also the
  *     kernel with warp-local passes; 2N <= 32: the element-pass kernel
- *     only; 2N = 192, 256: the cluster kernel only;
+ *     only; 2N = 192, 256: the cluster kernel with 1024 threads per CTA, or
+ *     with two row tasks per thread and register accumulation;
  *   - the persistent grid (blocks; at most the variant's residency);
  *   - the number of m-chunks per (cell, angle) work unit.
  * qbe_i3_shape reports the current shape and the number of variants

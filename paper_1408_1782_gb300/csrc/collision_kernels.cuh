@@ -567,13 +567,27 @@ __device__ __forceinline__ void cluster_sync_global() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// The cluster kernel's launch shapes: NT threads per CTA and the accumulation mode.  MODE 0: loop a
+// (outer), p (inner), each convolution's last stage adds eta_a S_a T into the unit's partial sum in
+// global memory (read-modify-write per convolution).  MODE 1: loop p (outer), a (inner), the last
+// stage accumulates over a in registers (each thread owns the same points in every convolution) and
+// the partial sum is written once per (m, p); NT = R B / 2, so that every thread owns two row tasks.
 template <int n>
-__global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3Cluster, 1024 / kThreadsI3Cluster)
+constexpr int i3_cluster_threads(int mode) {
+  return mode == 0 ? kThreadsI3Cluster : (n / kI3Cluster) * Split<n>::B / 2;
+}
+
+template <int n, int NT, int MODE>
+__global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(NT, 1)
     k_i3_cluster(const I3Jobs<float> jobs, float2* ws, const float2* __restrict__ gtw) {
-  static_assert(n / kI3Cluster * n >= kThreadsI3Cluster, "at least one element per thread in every phase");
+  static_assert(n / kI3Cluster * n >= NT, "at least one element per thread in every phase");
   using C2 = float2;
   constexpr int R = n / kI3Cluster, LS = n + 1, P = n * n;
   constexpr int XC = (n / 2) / kI3Cluster;           // Xi columns per CTA in the shift transforms
+  constexpr int A = Split<n>::A, B = Split<n>::B;
+  constexpr int TA = (R * B + NT - 1) / NT;          // row tasks (r, t2) per thread in an A stage
+  constexpr int TB = (R * A + NT - 1) / NT;          // tasks (r, k1) per thread in a B stage
+  static_assert(MODE == 0 || R * B == 2 * NT, "register accumulation: two row tasks per thread");
   static_assert(n % kI3Cluster == 0 && (n / 2) % kI3Cluster == 0, "cluster split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tw = reinterpret_cast<C2*>(smem_raw);
@@ -591,14 +605,133 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3C
       if (in) xcols[cnt++] = pos;
     }
   }
-  for (int pos = threadIdx.x; pos < n; pos += blockDim.x)
-    twT[(pos % Split<n>::A) * Split<n>::B + pos / Split<n>::A] = gtw[pos];
+  for (int pos = threadIdx.x; pos < n; pos += NT) twT[(pos % A) * B + pos / A] = gtw[pos];
   load_twiddles<n>(tw, gtw);
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x;
   const int rank = cluster_rank();
   const int r0 = rank * R;                           // this CTA's first row / column
   C2* Gs = ws + (size_t)cluster_index() * 3 * P;     // the cluster's transform field
   C2* Sig = Gs + P;                                  // the two shifted pairs
+  // One Psi'_j convolution of the field load(idx) (idx = r n + y, r a row of this CTA), with the
+  // last stage's results handed to epi(i, t1, idx, v) (i: the thread's row task, t1: its element).
+  // Between the passes the cluster's field is stored transposed, Gs'[ky][x] (ky in the row
+  // transform's permuted order): the row passes reach it from stage B (lanes = consecutive rows of
+  // this CTA) and the line pass from stage A (contiguous in x), so every global access is inside a
+  // line stage and coalesced.
+  auto convolve = [&](auto load, auto epi) {
+#pragma unroll
+    for (int i = 0; i < TA; ++i) {                   // forward rows: stage A loads the product
+      const int task = tid + i * NT;
+      if (TA * NT == R * B || task < R * B) {
+        const int r = task / B, t2 = task % B;
+        C2 v[A];
+#pragma unroll
+        for (int t1 = 0; t1 < A; ++t1) v[t1] = load(r * n + B * t1 + t2);
+        dft<A, -1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], twT[k1 * B + t2]);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) F[r * LS + B * k1 + t2] = v[k1];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TB; ++i) {
+      const int task = tid + i * NT;
+      if (TB * NT == R * A || task < R * A) {
+        const int r = task % R, k1 = task / R;
+        C2 b[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) b[t] = F[r * LS + B * k1 + t];
+        dft<B, -1>(b);
+#pragma unroll
+        for (int t = 0; t < B; ++t) Gs[(size_t)(B * k1 + t) * n + r0 + r] = b[t];
+      }
+    }
+    cluster_sync_global();                           // all rows transformed
+    // psi' convolution along x on this CTA's lines ky in [r0, r0 + R)
+#pragma unroll
+    for (int i = 0; i < TA; ++i) {
+      const int task = tid + i * NT;
+      if (TA * NT == R * B || task < R * B) {
+        const int cc = task / B, t2 = task % B;
+        C2 v[A];
+#pragma unroll
+        for (int t1 = 0; t1 < A; ++t1) v[t1] = __ldcg(&Gs[(size_t)(r0 + cc) * n + B * t1 + t2]);
+        dft<A, -1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], twT[k1 * B + t2]);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) F[cc * LS + B * k1 + t2] = v[k1];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TB; ++i) {
+      const int task = tid + i * NT;
+      if (TB * NT == R * A || task < R * A) {
+        const int cc = task % R, k1 = task / R;
+        C2 b[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) b[t] = F[cc * LS + B * k1 + t];
+        dft<B, -1>(b);
+        float sc[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) sc[t] = psl[(B * k1 + t) * R + cc];
+        dft_scaled<B, 1>(b, sc);
+#pragma unroll
+        for (int t = 0; t < B; ++t) F[cc * LS + B * k1 + t] = b[t];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TA; ++i) {
+      const int task = tid + i * NT;
+      if (TA * NT == R * B || task < R * B) {
+        const int cc = task / B, t2 = task % B;
+        C2 v[A];
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) v[k1] = F[cc * LS + B * k1 + t2];
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2]);
+        dft<A, 1>(v);
+#pragma unroll
+        for (int t1 = 0; t1 < A; ++t1) Gs[(size_t)(r0 + cc) * n + B * t1 + t2] = v[t1];
+      }
+    }
+    cluster_sync_global();                           // all lines convolved
+    // inverse rows on this CTA's rows: stage B loads, stage A hands its results to the epilogue
+#pragma unroll
+    for (int i = 0; i < TB; ++i) {
+      const int task = tid + i * NT;
+      if (TB * NT == R * A || task < R * A) {
+        const int r = task % R, k1 = task / R;
+        C2 b[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) b[t] = __ldcg(&Gs[(size_t)(B * k1 + t) * n + r0 + r]);
+        dft<B, 1>(b);
+#pragma unroll
+        for (int t = 0; t < B; ++t) F[r * LS + B * k1 + t] = b[t];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TA; ++i) {
+      const int task = tid + i * NT;
+      if (TA * NT == R * B || task < R * B) {
+        const int r = task / B, t2 = task % B;
+        C2 v[A];
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) v[k1] = F[r * LS + B * k1 + t2];
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2]);
+        dft<A, 1>(v);
+#pragma unroll
+        for (int t1 = 0; t1 < A; ++t1) epi(i, t1, r * n + B * t1 + t2, v[t1]);
+      }
+    }
+    __syncthreads();
+  };
   for (int gunit = cluster_index(); gunit < jobs.total; gunit += cluster_count()) {
     const I3Job<float>& jb = jobs.job[i3_job_of(jobs, gunit)];
     const int unit = gunit - jb.unit_begin;
@@ -609,12 +742,16 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3C
     const int j = (unit / nmc) % J;
     const int mc = unit % nmc;
     C2* acc = jb.K3part + (size_t)unit * 2 * P;
-    for (int idx = tid; idx < R * n; idx += nt) {
-      acc[(size_t)r0 * n + idx] = zero2<float>();
-      acc[P + (size_t)r0 * n + idx] = zero2<float>();
+    if (MODE == 0) {
+      #pragma unroll 1
+      for (int idx = tid; idx < R * n; idx += NT) {
+        acc[(size_t)r0 * n + idx] = zero2<float>();
+        acc[P + (size_t)r0 * n + idx] = zero2<float>();
+      }
     }
     const float* __restrict__ psp = jb.psip_s + (size_t)j * P;
-    for (int idx = tid; idx < n * R; idx += nt) psl[idx] = psp[(idx / R) * n + r0 + idx % R];
+    #pragma unroll 1
+    for (int idx = tid; idx < n * R; idx += NT) psl[idx] = psp[(idx / R) * n + r0 + idx % R];
     __syncthreads();
     const C2* wf = jb.wfine + (size_t)c * 2 * P;
     const int m0 = mc * mch, m1 = min(M, m0 + mch);
@@ -626,13 +763,15 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3C
       for (int p = 0; p < 2; ++p) {
         const C2* in = what + ((size_t)c * 4 + p) * P;
         C2* S = Sig + (size_t)p * P;
-        for (int idx = tid; idx < n * XC; idx += nt) {
+        #pragma unroll 1
+        for (int idx = tid; idx < n * XC; idx += NT) {
           const int ix = idx / XC, cc = idx % XC, iy = xcols[rank * XC + cc];
           F[idx] = xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<float>();
         }
         __syncthreads();
         fft_lines<n, 1>(F, XC, 1, XC, tw);
-        for (int idx = tid; idx < n * XC; idx += nt) {
+        #pragma unroll 1
+        for (int idx = tid; idx < n * XC; idx += NT) {
           const int ix = idx / XC, cc = idx % XC;
           S[ix * n + xcols[rank * XC + cc]] = F[idx];
         }
@@ -642,124 +781,74 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(kThreadsI3C
       // row transforms over this CTA's rows (columns outside Xi are zero)
       for (int p = 0; p < 2; ++p) {
         C2* S = Sig + (size_t)p * P + (size_t)r0 * n;
-        for (int idx = tid; idx < R * n; idx += nt) {
+        #pragma unroll 1
+        #pragma unroll 1
+      for (int idx = tid; idx < R * n; idx += NT) {
           const int r = idx / n, iy = idx % n;
           F[r * LS + iy] = xmask[iy] ? __ldcg(&S[idx]) : zero2<float>();
         }
         __syncthreads();
         fft_lines<n, 1>(F, R, LS, 1, tw);
-        for (int idx = tid; idx < R * n; idx += nt) S[idx] = F[(idx / n) * LS + idx % n];
+        #pragma unroll 1
+        for (int idx = tid; idx < R * n; idx += NT) S[idx] = F[(idx / n) * LS + idx % n];
         __syncthreads();
       }
-      // from here on this CTA reads only its own rows of the shifted fields.  Between the passes the
-      // cluster's field is stored transposed, Gs'[ky][x] (ky in the row transform's permuted order):
-      // the row passes reach it from stage B (lanes = consecutive rows of this CTA) and the line pass
-      // from stage A (contiguous in x), so every global access is inside a line stage and coalesced.
-      constexpr int A = Split<n>::A, B = Split<n>::B;
-      for (int a = 0; a < 4; ++a) {
-        const C2* wa = wf + (size_t)(a >> 1) * P + (size_t)r0 * n;
-        const C2* Sa = Sig + (size_t)(a >> 1) * P + (size_t)r0 * n;
-        const bool im = (a & 1) != 0;
-        const bool pos_eta = (a == 0);   // eta_a = +1 for a = 0, -1 otherwise
+      // from here on this CTA reads only its own rows of the shifted fields
+      if constexpr (MODE == 0) {
+        for (int a = 0; a < 4; ++a) {
+          const C2* wa = wf + (size_t)(a >> 1) * P + (size_t)r0 * n;
+          const C2* Sa = Sig + (size_t)(a >> 1) * P + (size_t)r0 * n;
+          const bool im = (a & 1) != 0;
+          const bool pos_eta = (a == 0);   // eta_a = +1 for a = 0, -1 otherwise
+          for (int p = 0; p < 2; ++p) {
+            const C2* Sp = Sig + (size_t)p * P + (size_t)r0 * n;
+            C2* accp = acc + (size_t)p * P + (size_t)r0 * n;
+            convolve(
+                [&](int idx) {
+                  const C2 z = wa[idx];
+                  return cscale(Sp[idx], im ? z.y : z.x);
+                },
+                [&](int, int, int idx, C2 v) {
+                  const C2 sv = Sa[idx];
+                  const float f = im ? sv.y : sv.x;
+                  const C2 d = accp[idx];
+                  accp[idx] = pos_eta ? mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y))
+                                      : mk2(fmaT(-f, v.x, d.x), fmaT(-f, v.y, d.y));
+                });
+          }
+        }
+      } else {
+        const bool first_m = (m == m0);
         for (int p = 0; p < 2; ++p) {
           const C2* Sp = Sig + (size_t)p * P + (size_t)r0 * n;
           C2* accp = acc + (size_t)p * P + (size_t)r0 * n;
-          // forward row transforms of w_a S_pair on this CTA's rows: stage A loads the product
-          for (int task = tid; task < R * B; task += nt) {
-            const int r = task / B, t2 = task % B;
-            C2 v[A];
+          C2 racc[TA][A];
+          for (int a = 0; a < 4; ++a) {
+            const C2* wa = wf + (size_t)(a >> 1) * P + (size_t)r0 * n;
+            const C2* Sa = Sig + (size_t)(a >> 1) * P + (size_t)r0 * n;
+            const bool im = (a & 1) != 0;
+            const float eta = (a == 0) ? 1.f : -1.f;
+            convolve(
+                [&](int idx) {
+                  const C2 z = wa[idx];
+                  return cscale(Sp[idx], im ? z.y : z.x);
+                },
+                [&](int i, int t1, int idx, C2 v) {
+                  const C2 sv = Sa[idx];
+                  const float f = eta * (im ? sv.y : sv.x);
+                  if (a == 0) racc[i][t1] = mk2(f * v.x, f * v.y);
+                  else racc[i][t1] = mk2(fmaT(f, v.x, racc[i][t1].x), fmaT(f, v.y, racc[i][t1].y));
+                });
+          }
+#pragma unroll
+          for (int i = 0; i < TA; ++i) {
+            const int task = tid + i * NT, r = task / B, t2 = task % B;
 #pragma unroll
             for (int t1 = 0; t1 < A; ++t1) {
               const int idx = r * n + B * t1 + t2;
-              const C2 z = wa[idx];
-              v[t1] = cscale(Sp[idx], im ? z.y : z.x);
-            }
-            dft<A, -1>(v);
-#pragma unroll
-            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], twT[k1 * B + t2]);
-#pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) F[r * LS + B * k1 + t2] = v[k1];
-          }
-          __syncthreads();
-          for (int task = tid; task < R * A; task += nt) {
-            const int r = task % R, k1 = task / R;
-            C2 b[B];
-#pragma unroll
-            for (int t = 0; t < B; ++t) b[t] = F[r * LS + B * k1 + t];
-            dft<B, -1>(b);
-#pragma unroll
-            for (int t = 0; t < B; ++t) Gs[(size_t)(B * k1 + t) * n + r0 + r] = b[t];
-          }
-          cluster_sync_global();                     // all rows transformed
-          // psi' convolution along x on this CTA's lines ky in [r0, r0 + R)
-          for (int task = tid; task < R * B; task += nt) {
-            const int cc = task / B, t2 = task % B;
-            C2 v[A];
-#pragma unroll
-            for (int t1 = 0; t1 < A; ++t1) v[t1] = __ldcg(&Gs[(size_t)(r0 + cc) * n + B * t1 + t2]);
-            dft<A, -1>(v);
-#pragma unroll
-            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], twT[k1 * B + t2]);
-#pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) F[cc * LS + B * k1 + t2] = v[k1];
-          }
-          __syncthreads();
-          for (int task = tid; task < R * A; task += nt) {
-            const int cc = task % R, k1 = task / R;
-            C2 b[B];
-#pragma unroll
-            for (int t = 0; t < B; ++t) b[t] = F[cc * LS + B * k1 + t];
-            dft<B, -1>(b);
-            float sc[B];
-#pragma unroll
-            for (int t = 0; t < B; ++t) sc[t] = psl[(B * k1 + t) * R + cc];
-            dft_scaled<B, 1>(b, sc);
-#pragma unroll
-            for (int t = 0; t < B; ++t) F[cc * LS + B * k1 + t] = b[t];
-          }
-          __syncthreads();
-          for (int task = tid; task < R * B; task += nt) {
-            const int cc = task / B, t2 = task % B;
-            C2 v[A];
-#pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) v[k1] = F[cc * LS + B * k1 + t2];
-#pragma unroll
-            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2]);
-            dft<A, 1>(v);
-#pragma unroll
-            for (int t1 = 0; t1 < A; ++t1) Gs[(size_t)(r0 + cc) * n + B * t1 + t2] = v[t1];
-          }
-          cluster_sync_global();                     // all lines convolved
-          // inverse row transforms on this CTA's rows: stage B loads, stage A accumulates eta_a S_a
-          for (int task = tid; task < R * A; task += nt) {
-            const int r = task % R, k1 = task / R;
-            C2 b[B];
-#pragma unroll
-            for (int t = 0; t < B; ++t) b[t] = __ldcg(&Gs[(size_t)(B * k1 + t) * n + r0 + r]);
-            dft<B, 1>(b);
-#pragma unroll
-            for (int t = 0; t < B; ++t) F[r * LS + B * k1 + t] = b[t];
-          }
-          __syncthreads();
-          for (int task = tid; task < R * B; task += nt) {
-            const int r = task / B, t2 = task % B;
-            C2 v[A];
-#pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) v[k1] = F[r * LS + B * k1 + t2];
-#pragma unroll
-            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2]);
-            dft<A, 1>(v);
-#pragma unroll
-            for (int t1 = 0; t1 < A; ++t1) {
-              const int idx = r * n + B * t1 + t2;
-              const C2 sv = Sa[idx];
-              const float f = im ? sv.y : sv.x;
-              const C2 d = accp[idx];
-              accp[idx] = pos_eta ? mk2(fmaT(f, v[t1].x, d.x), fmaT(f, v[t1].y, d.y))
-                                  : mk2(fmaT(-f, v[t1].x, d.x), fmaT(-f, v[t1].y, d.y));
+              accp[idx] = first_m ? racc[i][t1] : cadd(accp[idx], racc[i][t1]);
             }
           }
-          __syncthreads();
         }
       }
     }
@@ -872,7 +961,8 @@ size_t i3_staged_smem_bytes() {
 //     0: (256, 64 KB, 3)   1: (128, 32 KB, 6);  k_i3_sf 2: (256, 64 KB, 3)   3: (128, 32 KB, 6)
 //   FP32, n = 64, 96, 128: 0, 1, 2: the fused shared-memory kernel in the FusedShapes<n> shapes,
 //     3: k_i3_smem (1024 threads, element passes through shared memory)
-//   FP32, n <= 32: k_i3_smem;  FP32, n > 128: the cluster kernel.
+//   FP32, n <= 32: k_i3_smem;  FP32, n > 128: the cluster kernel, 0: 1024 threads per CTA with a
+//     partial-sum update per convolution, 1: two row tasks per thread with register accumulation.
 struct I3Launch {
   const void* fn = nullptr;
   int threads = 0;
@@ -884,7 +974,7 @@ struct I3Launch {
 template <int n, class T>
 constexpr int i3_nvariants() {
   if constexpr (std::is_same<T, float>::value) {
-    if constexpr (use_i3_cluster<n>()) return 1;
+    if constexpr (use_i3_cluster<n>()) return 2;
     else if constexpr (use_i3_fused<n>()) return n == kWlN ? 5 : 4;   // 128 points: + k_i3_wl
     else return 1;
   } else {
@@ -896,8 +986,14 @@ template <int n, class T>
 I3Launch i3_variant(int v) {
   I3Launch l;
   if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
-    l = {(const void*)k_i3_cluster<n>, kThreadsI3Cluster, i3_cluster_smem_bytes<n>(), true,
-         "cluster of 4 CTAs x 1024 threads"};
+    constexpr int NT1 = i3_cluster_threads<n>(1);
+    if (v == 1)
+      l = {(const void*)k_i3_cluster<n, NT1, 1>, NT1, i3_cluster_smem_bytes<n>(), true,
+           n == 256 ? "cluster of 4 CTAs x 512 threads, register accumulation"
+                    : "cluster of 4 CTAs x 384 threads, register accumulation"};
+    else
+      l = {(const void*)k_i3_cluster<n, kThreadsI3Cluster, 0>, kThreadsI3Cluster, i3_cluster_smem_bytes<n>(), true,
+           "cluster of 4 CTAs x 1024 threads"};
   } else if constexpr (std::is_same<T, float>::value && use_i3_fused<n>()) {
     using S = FusedShapes<n>;
     constexpr const char* names[3] = {"fused, per-convolution partial sums", "fused, register accumulation",
@@ -947,25 +1043,28 @@ void set_smem_attributes() {
   }
 }
 
-// Clusters of k_i3_cluster<n> that can be resident at once on the current device (cached per device).
+// Clusters of the cluster variant v of k_i3_cluster<n> that can be resident at once on the current
+// device (cached per device and variant).
 template <int n>
-int i3_max_clusters() {
-  static int cached[64] = {};
+int i3_max_clusters(int v) {
+  static int cached[64][2] = {};
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
-  if (cached[dev & 63] > 0) return cached[dev & 63];
+  v = (v == 1) ? 1 : 0;
+  if (cached[dev & 63][v] > 0) return cached[dev & 63][v];
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const I3Launch l = i3_variant<n, float>(v);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kI3Cluster * (nsm > 0 ? nsm : 1));
-  cfg.blockDim = dim3(kThreadsI3Cluster);
-  cfg.dynamicSmemBytes = i3_cluster_smem_bytes<n>();
+  cfg.blockDim = dim3(l.threads);
+  cfg.dynamicSmemBytes = l.smem;
   int ncl = 0;
-  if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_i3_cluster<n>, &cfg) != cudaSuccess || ncl < 1) {
+  if (cudaOccupancyMaxActiveClusters(&ncl, l.fn, &cfg) != cudaSuccess || ncl < 1) {
     cudaGetLastError();
     ncl = (nsm > 0 ? nsm : 1) / kI3Cluster;
   }
-  cached[dev & 63] = ncl < 1 ? 1 : ncl;
-  return cached[dev & 63];
+  cached[dev & 63][v] = ncl < 1 ? 1 : ncl;
+  return cached[dev & 63][v];
 }
 
 // Resident blocks per SM of an I3 variant (at least 1).
@@ -979,7 +1078,7 @@ int i3_blocks_per_sm(int v) {
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    b = (i3_max_clusters<n>() * kI3Cluster + nsm - 1) / (nsm > 0 ? nsm : 1);
+    b = (i3_max_clusters<n>(v) * kI3Cluster + nsm - 1) / (nsm > 0 ? nsm : 1);
   } else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, l.fn, l.threads, l.smem) != cudaSuccess) {
     cudaGetLastError();
     b = 1;
@@ -996,9 +1095,12 @@ int i3_variant_count() {
 // launch in ms for variants 0..3 (J = M = 32): N = 16, 128 cells 136.8 136.2 132.9 129.4;
 // N = 32, 128 cells 652.2 640.5 625.3 630.4; N = 48, 64 cells 868.4 886.2 860.3 879.5; N = 64,
 // 32 cells 752.1 760.2 732.5 742.2; N = 128, 8 cells 897.0 902.9 885.5 901.9.
+// FP32 cluster kernel (I3 launch, J = M = 32): N = 128, 32 cells 231.7 ms (variant 0), 192.4 ms
+// (variant 1); N = 96, 64 cells 217.6 and 208.9 ms.
 template <int n, class T>
 int i3_default_variant() {
   if constexpr (std::is_same<T, float>::value && use_i3_fused<n>()) return FusedShapes<n>::DEFAULT;
+  else if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) return 1;
   else if constexpr (std::is_same<T, double>::value) return 2;
   else return 0;
 }
@@ -1012,7 +1114,7 @@ int i3_variant_concurrency(int v, int grid, int total) {
   int g = total < grid ? total : grid;
   if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
     int ncl = grid / kI3Cluster;
-    const int cmax = i3_max_clusters<n>();
+    const int cmax = i3_max_clusters<n>(v);
     if (ncl > cmax) ncl = cmax;
     if (ncl > total) ncl = total;
     g = ncl < 1 ? 1 : ncl;
@@ -1131,7 +1233,7 @@ cudaError_t i3_group_n(const Tables* const* tabs, const CollisionWork* const* cw
   int g = total < grid ? total : grid;
   if constexpr (std::is_same<T, float>::value && use_i3_cluster<n>()) {
     int ncl = grid / kI3Cluster;
-    const int cmax = i3_max_clusters<n>();
+    const int cmax = i3_max_clusters<n>(v);
     if (ncl > cmax) ncl = cmax;
     if (ncl > total) ncl = total;
     if (ncl < 1) ncl = 1;

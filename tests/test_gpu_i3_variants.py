@@ -51,14 +51,17 @@ def test_fp64_variants_match_oracle(qbe, N, J, M, ncells):
         assert np.abs(got - ref).max() < TOL_F64 * np.abs(ref).max(), v
 
 
-@pytest.mark.parametrize("N,J,M,ncells", [(32, 8, 6, 3), (48, 4, 4, 2), (64, 8, 6, 3)])
+@pytest.mark.parametrize("N,J,M,ncells", [(32, 8, 6, 3), (48, 4, 4, 2), (64, 8, 6, 3), (96, 4, 3, 2),
+                                           (128, 2, 3, 2)])
 def test_fp32_variants_match_fp64(qbe, N, J, M, ncells):
-    """The fused kernel in both shapes and the element-pass kernel (N = 32, 48, 64: padded grids of
-    64, 96 and 128 points), several (cell, j, m-chunk) units per block."""
+    """The fused kernel in its shapes and the element-pass kernel (N = 32, 48, 64: padded grids of
+    64, 96 and 128 points; at 128 also the warp-local kernel), several (cell, j, m-chunk) units per
+    block; the cluster kernel in both shapes (N = 96, 128: 192 and 256 points), several units and
+    several m per cluster."""
     w = inputs.synthetic_w(N, ncells, seed=50 + N, perturb=0.05)
     ref = _collide_all_variants(qbe, w, N, J, M, 0)[0]
     res = _collide_all_variants(qbe, w, N, J, M, 1)
-    assert len(res) == (5 if N == 64 else 4)
+    assert len(res) == {64: 5, 96: 2, 128: 2}.get(N, 4)
     for v, got in res.items():
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err < TOL_F32, (v, err)
