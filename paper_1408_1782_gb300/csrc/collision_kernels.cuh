@@ -505,7 +505,7 @@ template <> struct FusedShapes<64> {
 template <> struct FusedShapes<96> {
   static constexpr int T0 = 768, B0 = 1, M0 = 0, T1 = 768, B1 = 1, M1 = 2, T2 = 384, B2 = 2, M2 = 2, DEFAULT = 3;
 };
-template <> struct FusedShapes<128> {   // variant 4: k_i3_wl, 94.9 ms (shape 0: 101.1 ms)
+template <> struct FusedShapes<128> {   // variant 4: k_i3_wl, 92.3 ms (shape 0: 101.1 ms)
   static constexpr int T0 = 512, B0 = 1, M0 = 1, T1 = 1024, B1 = 1, M1 = 2, T2 = 1024, B2 = 1, M2 = 0, DEFAULT = 4;
 };
 
@@ -796,25 +796,20 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(NT, 1)
       // from here on this CTA reads only its own rows of the shifted fields
       if constexpr (MODE == 0) {
         for (int a = 0; a < 4; ++a) {
-          const C2* wa = wf + (size_t)(a >> 1) * P + (size_t)r0 * n;
-          const C2* Sa = Sig + (size_t)(a >> 1) * P + (size_t)r0 * n;
-          const bool im = (a & 1) != 0;
-          const bool pos_eta = (a == 0);   // eta_a = +1 for a = 0, -1 otherwise
+          // component im of the fine pair and of the shifted pair, loaded as single floats
+          const int im = a & 1;
+          const float* wa = reinterpret_cast<const float*>(wf + (size_t)(a >> 1) * P + (size_t)r0 * n) + im;
+          const float* Sa = reinterpret_cast<const float*>(Sig + (size_t)(a >> 1) * P + (size_t)r0 * n) + im;
+          const float eta = (a == 0) ? 1.f : -1.f;
           for (int p = 0; p < 2; ++p) {
             const C2* Sp = Sig + (size_t)p * P + (size_t)r0 * n;
             C2* accp = acc + (size_t)p * P + (size_t)r0 * n;
-            convolve(
-                [&](int idx) {
-                  const C2 z = wa[idx];
-                  return cscale(Sp[idx], im ? z.y : z.x);
-                },
-                [&](int, int, int idx, C2 v) {
-                  const C2 sv = Sa[idx];
-                  const float f = im ? sv.y : sv.x;
-                  const C2 d = accp[idx];
-                  accp[idx] = pos_eta ? mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y))
-                                      : mk2(fmaT(-f, v.x, d.x), fmaT(-f, v.y, d.y));
-                });
+            convolve([&](int idx) { return cscale(Sp[idx], wa[2 * idx]); },
+                     [&](int, int, int idx, C2 v) {
+                       const float f = eta * Sa[2 * idx];
+                       const C2 d = accp[idx];
+                       accp[idx] = mk2(fmaT(f, v.x, d.x), fmaT(f, v.y, d.y));
+                     });
           }
         }
       } else {
@@ -1095,7 +1090,7 @@ int i3_variant_count() {
 // launch in ms for variants 0..3 (J = M = 32): N = 16, 128 cells 136.8 136.2 132.9 129.4;
 // N = 32, 128 cells 652.2 640.5 625.3 630.4; N = 48, 64 cells 868.4 886.2 860.3 879.5; N = 64,
 // 32 cells 752.1 760.2 732.5 742.2; N = 128, 8 cells 897.0 902.9 885.5 901.9.
-// FP32 cluster kernel (I3 launch, J = M = 32): N = 128, 32 cells 231.7 ms (variant 0), 192.4 ms
+// FP32 cluster kernel (I3 launch, J = M = 32): N = 128, 32 cells 219.1 ms (variant 0), 192.4 ms
 // (variant 1); N = 96, 64 cells 217.6 and 208.9 ms.
 template <int n, class T>
 int i3_default_variant() {

@@ -438,9 +438,10 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_i3_wl(const I3Jobs<float> job
         C2* accp = acc + (size_t)p * P;
         C2 racc[TPT][A];
         for (int a = 0; a < 4; ++a) {
-          const C2* __restrict__ wa = wf + (size_t)(a >> 1) * P;
-          const C2* Sa = Sig + (size_t)(a >> 1) * P;
-          const bool im = (a & 1) != 0;
+          // component im of the fine pair and of the shifted pair, loaded as single floats
+          const int im = a & 1;
+          const float* __restrict__ wa = reinterpret_cast<const float*>(wf + (size_t)(a >> 1) * P) + im;
+          const float* Sa = reinterpret_cast<const float*>(Sig + (size_t)(a >> 1) * P) + im;
           // forward rows of w_a Sigma_p (warp-local): stage A loads the product, stage B
 #pragma unroll
           for (int k = 0; k < TPT; ++k) {
@@ -449,8 +450,7 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_i3_wl(const I3Jobs<float> job
 #pragma unroll
             for (int t1 = 0; t1 < A; ++t1) {
               const int idx = x * n + B * t1 + t2r;
-              const C2 z = wa[idx];
-              v[t1] = cscale(Sp[idx], im ? z.y : z.x);
+              v[t1] = cscale(Sp[idx], wa[2 * idx]);
             }
             dft<A, -1>(v);
 #pragma unroll
@@ -493,10 +493,7 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_i3_wl(const I3Jobs<float> job
             const int x = row_of(k);
             float f[A];
 #pragma unroll
-            for (int t1 = 0; t1 < A; ++t1) {
-              const C2 sv = Sa[x * n + B * t1 + t2r];
-              f[t1] = eta * (im ? sv.y : sv.x);
-            }
+            for (int t1 = 0; t1 < A; ++t1) f[t1] = eta * Sa[2 * (x * n + B * t1 + t2r)];
             C2 v[A];
 #pragma unroll
             for (int k1 = 0; k1 < A; ++k1) v[k1] = G[wl_addr(x, B * k1 + t2r)];
