@@ -50,9 +50,11 @@ SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (an issue-rate microbenchmark)
 FP32_FMA_PER_CLK_PER_SM = 128        # measured 116 FFMA/clk/SM
 # DRAM bytes (read + write) per (cell, j, m) unit of the default I3 kernel from one ncu capture of a
-# slice (8 cells at N = 64: k_i3_sf in FP64, k_i3_fused in FP32; 4 cells at N = 128: k_i3_cluster),
-# scaled by units; absent for sizes with no capture of the current kernel.
-I3_DRAM_BYTES_PER_UNIT = {(64, 0): 113.540e9 / 8192, (64, 1): 3.228e9 / 8192, (128, 1): 28.305e9 / 4096}
+# slice (8 cells at N = 64: k_i3_sf in FP64, k_i3_wl in FP32; 4 cells at N = 128: k_i3_cluster in its
+# register-accumulating shape), scaled by units; absent for sizes with no capture of the current kernel.
+I3_DRAM_BYTES_PER_UNIT = {(64, 0): 113.540e9 / 8192, (64, 1): 3.080e9 / 8192, (128, 1): 15.105e9 / 4096}
+# The same for the default I3 transpose kernel (8 cells at N = 64: k_i3_vjp_wl, one cotangent).
+I3_VJP_DRAM_BYTES_PER_UNIT = {(64, 1): 5.942e9 / 8192}
 
 
 def workload(name="plain_fp64_n64", precision=None):
@@ -782,6 +784,7 @@ def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clock
     for _ in range(warmup):
         gradient()
     torch.cuda.synchronize()
+    vjp_variant = s.vjp_i3_variant()[0]
     sampler = ClockSampler(gpu_uuid(local)) if clocks else None
     s.enable_timing(True)
     launches0 = s.launch_count()
@@ -828,6 +831,9 @@ def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clock
     t2 = time.perf_counter()
     cpu = adjoint_cpu_baseline(wl) if cpu_baseline else None
     conf = config_dict(wl, 1)
+    vjp_kernel = "k_i3_vjp"                            # the staged form (FP64; FP32 above 128 points)
+    if prec == 1 and 2 * N <= 128:
+        vjp_kernel = "k_i3_vjp_wl" if (2 * N == 128 and kgrp == 1 and vjp_variant == 0) else "k_i3_vjp_smem"
     how = ("full tape: every intermediate state kept" if tape == "full"
            else f"checkpoint every {every}, segments recomputed")
     conf.update({"horizon_steps": H, "tape": tape, "checkpoint_every": every if tape != "full" else None,
@@ -843,9 +849,11 @@ def measure_adjoint(wl, local, H, every, steps, warmup, cpu_baseline=True, clock
         "reverse_ms_per_split_step_both_gradients": rev / steps / H,
         "gradients_per_s": 2e3 * steps / (fwd + rev),
         "observables": obs.cpu().tolist(),
-        "roofline": {"kernel": "k_i3_vjp (transpose of the Hu-Ying I3 term)", "bound": "alu",
+        "roofline": {"kernel": f"{vjp_kernel} (transpose of the Hu-Ying I3 term)", "bound": "alu",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "flops_per_launch": flops, "avg_launch_ms": avg_vi3 * 1e3,
+                     "traffic": (I3_VJP_DRAM_BYTES_PER_UNIT[(N, prec)] * Nx * wl["J"] * wl["M"]
+                                 if (N, prec) in I3_VJP_DRAM_BYTES_PER_UNIT and kgrp == 1 else None),
+                     "flops_per_launch": flops, "avg_launch_ms": avg_vi3 * 1e3,
                      "peak_source": (f"derived: {SM_COUNT} SMs x {lanes} {'FP64' if prec == 0 else 'FP32'} "
                                      f"FMA/clk x 2 flop x {sm_max:.0f} MHz")},
         "kernel_ms": {k: round(v, 2) for k, v in groups.items()},
