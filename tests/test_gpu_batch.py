@@ -16,6 +16,7 @@ CASES = [  # N, Nx, bc, precision
     (48, 2, "maxwell", 0),
     (96, 2, "maxwell", 1),
     (128, 2, "periodic", 1),
+    (128, 3, "maxwell", 1),    # a second member of the 256-point group: two jobs in one cluster work queue
 ]
 
 
