@@ -319,6 +319,24 @@ def test_full_tape_equals_checkpointed_tape(qbe, precision):
     s.close()
 
 
+def test_full_tape_that_does_not_fit_fails_cleanly(qbe):
+    """A full tape larger than the device memory: QBE_ERR_ALLOC before any step, the state unchanged,
+    no valid tape afterwards; a checkpointed tape still works on the same handle."""
+    N, Nx = 16, 4
+    W = inputs.synthetic_w(N, Nx, seed=64, perturb=0.05)
+    s = qbe.Solver(N, Nx, J=4, M=2)
+    s.set_state(W)
+    with pytest.raises(qbe.QbeError):
+        s.step_taped(0.01, 2_000_000_000)        # about 2.6e14 bytes of intermediate states
+    assert np.array_equal(s.get_state(), W)
+    with pytest.raises(qbe.QbeError):
+        s.step_vjp(np.zeros_like(W))
+    s.step_checkpointed(0.01, 2, 1)
+    lam0, _ = s.step_vjp(inputs.random_field(W.shape, seed=65))
+    assert np.isfinite(lam0).all()
+    s.close()
+
+
 def observables_grad(s, W, B, dt, nsteps, every):
     s.set_state(W)
     s.set_bfield(B)
