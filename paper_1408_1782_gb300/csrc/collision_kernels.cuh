@@ -524,9 +524,11 @@ template <> struct FusedShapes<128> {   // variant 4: k_i3_wl, 92.3 ms (shape 0:
 // --------------------------------------------------------------------------
 // Measured at N = 128 (32 cells, C[W] I3 launch), element passes through shared memory around
 // every global access: 4 CTAs x 1024 threads 239.9 ms; 8 CTAs x 512 threads (two CTAs of
-// different clusters per SM) 255.4 ms; the staged k_i3 294.5 ms.
+// different clusters per SM) 255.4 ms; the staged k_i3 294.5 ms.  With the line stages reading
+// and writing the transposed field directly: 219.1 ms (1024 threads, mode 0 below), 192.4 ms
+// (512 threads, mode 1).
 constexpr int kI3Cluster = 4;             // CTAs per cluster
-constexpr int kThreadsI3Cluster = 1024;   // threads per CTA
+constexpr int kThreadsI3Cluster = 1024;   // threads per CTA of mode 0
 
 template <int n>
 __host__ __device__ constexpr bool use_i3_cluster() {
