@@ -236,10 +236,12 @@ cudaError_t collide_vjp(const Tables& t, CollisionWork& cw, VjpWork& vw, const d
 // Cotangents one collision product should carry.  The staged transpose kernels (FP64, and FP32 on
 // grids above 128 points) are bound by their transforms, so sharing the state's Psi' convolutions saves
 // about a quarter of the work per product at two cotangents (measured: FP64, N = 64, 16 cells, 847 ms
-// per single launch against 1297 ms for two).  The FP32 shared-memory kernel runs its transforms on chip
-// and is bound by its global accumulators; every further cotangent adds three fields of them per block,
-// which pushes the working set out of L2 (two cotangents: 685 ms against 2 x 333 ms, L2 hit rate 85 %
-// -> 68 %), so it takes one cotangent at a time.
+// per single launch against 1297 ms for two).  The FP32 shared-memory kernels run their transforms on
+// chip: the element-pass kernel is bound by its global accumulators, and every further cotangent adds
+// three fields of them per block, which pushes the working set out of L2 (two cotangents: 685 ms
+// against 2 x 333 ms, L2 hit rate 85 % -> 68 %); the warp-local kernel (128 points) holds one
+// cotangent's shifted-back sums in registers, which leave no room for a second.  Both take one
+// cotangent at a time.
 int vjp_cotangent_group(const Tables& t, int prec) { return (prec == 1 && t.n <= 128) ? 1 : kMaxCotangents; }
 
 int vjp_i3_variants(int n, int prec) { return (prec == 1 && n == 128) ? 2 : 1; }
