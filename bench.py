@@ -20,6 +20,7 @@ with a checkpoint every step recomputed by the reverse sweep.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --mode collide [--cells C]   # time C[W] alone on the first C cells
   python bench.py --mode vjp [--cells C]       # time the collision VJP alone
+  python bench.py --mode peaks                 # measured FP64 / FP32 arithmetic issue rates
 
 --mode collide (not the benchmark line; used for profiling) times only the
 collision operator, one evaluation of the first C cells per step.
@@ -47,8 +48,8 @@ sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
-FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 1.90 DFMA/clk/SM (an issue-rate microbenchmark)
-FP32_FMA_PER_CLK_PER_SM = 128        # measured 116 FFMA/clk/SM
+FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 2.00 DFMA lanes/clk/SM (bench.py --mode peaks)
+FP32_FMA_PER_CLK_PER_SM = 128        # measured 122 FFMA lanes/clk/SM (the same run)
 # DRAM bytes (read + write) per (cell, j, m) unit of the default I3 kernel from one ncu capture of a
 # slice (8 cells at N = 64: k_i3_sf in FP64, k_i3_wl in FP32; 4 cells at N = 128: k_i3_cluster in its
 # register-accumulating shape), scaled by units; absent for sizes with no capture of the current kernel.
@@ -251,6 +252,8 @@ def run_ours(args):
     g.build()
     from paper_1408_1782_gb300 import decomp, inputs, qbe
 
+    if args.mode == "peaks":
+        return run_peaks(local)
     if args.workload in ("batched_16", "batched_64"):
         return run_batched(args, local, full=args.workload == "batched_64")
     if args.workload == "adjoint_n64":
@@ -389,8 +392,8 @@ def run_ours(args):
                                      if (N, prec) in I3_DRAM_BYTES_PER_UNIT else None),
                          "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_i3_s * 1e3,
                          "peak_source": (f"derived: {SM_COUNT} SMs x {lanes} {'FP64' if prec == 0 else 'FP32'} FMA/clk x 2 "
-                                         f"flop x {sm_max:.0f} MHz (microbenchmark: DFMA 1.20 TFLOP/s, FFMA 73.1 "
-                                         f"TFLOP/s at 2002 MHz)")},
+                                         f"flop x {sm_max:.0f} MHz (bench.py --mode peaks at 2070 MHz: DFMA 1.256, "
+                                         f"FFMA 76.8 TFLOP/s)")},
             "kernel_share": {k: round(v["ms"] / total_group_ms, 4) for k, v in groups.items()},
             "streaming_kernels": streaming,
             "cpu_baseline": cpu,
@@ -641,6 +644,31 @@ def run_batched(args, local, full=False):
     b.close()
     for s in sims:
         s.close()
+    return 0
+
+
+def run_peaks(local):
+    """Arithmetic issue rates of the GPU (qbe_arith_issue_rates), per second and per clock per SM at
+    the SM clock sampled while they ran: the measurement behind the derived "alu" peaks."""
+    import torch
+
+    from paper_1408_1782_gb300 import qbe
+
+    stream = torch.cuda.current_stream()
+    qbe.arith_issue_rates(local, stream)          # warm-up (clocks, module load)
+    sampler = ClockSampler(gpu_uuid(local))
+    sampler.start()
+    runs = [qbe.arith_issue_rates(local, stream) for _ in range(20)]   # about 1.5 s for the clock samples
+    clk = sampler.stop()
+    rates = {k: statistics.median(r[k] for r in runs) for k in runs[0]}
+    mhz = clk.get("sm_mhz") or measured_sm_max()
+    line = {"mode": "peaks", "lane_ops_per_s": rates,
+            "per_clk_per_sm": {k: v / (SM_COUNT * mhz * 1e6) for k, v in rates.items()},
+            "fp64_fma_tflops": 2 * rates["dfma"] / 1e12, "fp32_fma_tflops": 2 * rates["ffma"] / 1e12,
+            "derived_peaks_tflops": {"fp64": SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * measured_sm_max() / 1e6,
+                                     "fp32": SM_COUNT * FP32_FMA_PER_CLK_PER_SM * 2 * measured_sm_max() / 1e6},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -956,7 +984,7 @@ def main():
                     help="default workload: skip the FP32-split and adjoint measurements of the same grid")
     ap.add_argument("--forms-horizon", type=int, default=2,
                     help="split steps of the adjoint measurement inside the default line")
-    ap.add_argument("--mode", choices=["step", "collide", "vjp"], default="step")
+    ap.add_argument("--mode", choices=["step", "collide", "vjp", "peaks"], default="step")
     ap.add_argument("--workload", choices=["plain_fp64_n64", "precision_n128", "batched_16", "batched_64",
                                            "adjoint_n64"],
                     default="plain_fp64_n64")

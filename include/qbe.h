@@ -306,6 +306,17 @@ long long qbe_launch_count(const qbe_handle* h);
 int qbe_enable_timing(qbe_handle* h, int enable);
 int qbe_kernel_time(qbe_handle* h, int which, double* total_ms, long long* launches);
 
+/* Arithmetic issue rates of the device (measurement behind the "alu"
+ * rooflines; not part of the method).  Runs, on `stream` (a cudaStream_t;
+ * NULL: the default stream) of device `device`, kernels of 8 blocks of 256
+ * threads per SM whose threads each advance eight independent chains of one
+ * operation, one warm-up and one timed launch each, and writes
+ * rates[0..3] = FP64 fma, FP64 add, FP64 mul and FP32 fma lane-operations
+ * per second.  Synchronises the stream; allocates and frees about 2.5 MB of
+ * device memory.  Errors: QBE_ERR_ARG (rates NULL, device < 0),
+ * QBE_ERR_CUDA. */
+int qbe_arith_issue_rates(int device, void* stream, double* rates);
+
 /* Launch shape of the I3 (Hu-Ying term, eq. approxH-JM) kernel -- the dominant
  * part of C[W] (Sec. 3.2) -- and its autotuner.  A shape is
  *   - a launch variant: one of the kernel forms instantiated for this padded

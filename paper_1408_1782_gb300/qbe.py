@@ -93,6 +93,7 @@ SIGNATURES = {
     "qbe_i3_variant_name": (ctypes.c_char_p, [_c_void_p, _c_int]),
     "qbe_set_i3_shape": (_c_int, [_c_void_p, _c_int, _c_int, _c_int]),
     "qbe_autotune": (_c_int, [_c_void_p, ctypes.POINTER(_c_double)]),
+    "qbe_arith_issue_rates": (_c_int, [_c_int, _c_void_p, ctypes.POINTER(_c_double)]),
     "qbe_vjp_i3_variant": (_c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "qbe_set_vjp_i3_variant": (_c_int, [_c_void_p, _c_int]),
     "qbe_batch_create": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, ctypes.POINTER(_c_void_p)]),
@@ -504,6 +505,17 @@ class Solver:
 
     def set_vjp_i3_variant(self, variant=-1):
         self._check(lib().qbe_set_vjp_i3_variant(self._h, int(variant)), "qbe_set_vjp_i3_variant")
+
+
+def arith_issue_rates(device=0, stream=None):
+    """Measured FP64 fma / add / mul and FP32 fma lane-operations per second of the device
+    (qbe_arith_issue_rates); `stream` a torch.cuda.Stream or None."""
+    out = (_c_double * 4)()
+    h = _c_void_p(getattr(stream, "cuda_stream", stream))
+    rc = lib().qbe_arith_issue_rates(int(device), h, out)
+    if rc != 0:
+        raise QbeError(f"qbe_arith_issue_rates failed ({rc})")
+    return {"dfma": out[0], "dadd": out[1], "dmul": out[2], "ffma": out[3]}
 
 
 def fd_fit_moments(rho4, mom, energy) -> QbeFermiDirac:

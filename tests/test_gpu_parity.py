@@ -296,3 +296,13 @@ def test_plain_fp64_n64_sampled_cells_match_stored_oracle(qbe):
     for i, c in enumerate(cells):
         assert np.abs(rho[c] - rho_ref[i]).max() < TOL_C * scale[c]
     assert np.all(np.abs(rho).max(axis=1) < 1e-5 * scale)
+
+
+def test_arith_issue_rates_are_measured(qbe):
+    """qbe_arith_issue_rates (the measurement behind the derived FP64 / FP32 peaks): positive rates,
+    FP32 fma far above FP64 fma on this part, and FP64 fma below four lanes per clock per SM at the
+    2070 MHz maximum clock (twice the unit count the FP64 peak is derived from)."""
+    r = qbe.arith_issue_rates(0)
+    assert all(v > 0 for v in r.values())
+    assert r["ffma"] > 10 * r["dfma"]
+    assert r["dfma"] < 152 * 4 * 2.07e9
