@@ -505,7 +505,7 @@ template <> struct FusedShapes<64> {
 template <> struct FusedShapes<96> {
   static constexpr int T0 = 768, B0 = 1, M0 = 0, T1 = 768, B1 = 1, M1 = 2, T2 = 384, B2 = 2, M2 = 2, DEFAULT = 3;
 };
-template <> struct FusedShapes<128> {   // variant 4: k_i3_wl, 92.3 ms (shape 0: 101.1 ms)
+template <> struct FusedShapes<128> {   // variant 4: k_i3_wl, 88.8 ms (shape 0: 101.1 ms)
   static constexpr int T0 = 512, B0 = 1, M0 = 1, T1 = 1024, B1 = 1, M1 = 2, T2 = 1024, B2 = 1, M2 = 0, DEFAULT = 4;
 };
 

@@ -234,6 +234,28 @@ __device__ __forceinline__ void dft_scaled(C2 (&a)[R], const typename RealOf<C2>
   for (int i = 0; i < R; ++i) a[i] = b[i];
 }
 
+// DFT of length 16 whose inputs a[4..11] are zero -- a stage-B line of the 128-point padded grid
+// holding only band-limited (Xi) frequencies -- with the first radix-2 stage reduced to copies: its
+// butterflies pair a[r] with a[r + 8], r < 8, and one of the two is zero.
+template <int SIGN, class C2>
+__device__ __forceinline__ void dft16_xi(C2 (&a)[16]) {
+  C2 b[16];
+#pragma unroll
+  for (int g = 0; g < 16; g += 2) {
+    const int r = bitrev(g, 4);   // 0..7; bitrev(g + 1, 4) = r + 8
+    if (r < 4) {
+      b[g] = a[r];
+      b[g + 1] = a[r];
+    } else {
+      b[g] = a[r + 8];
+      b[g + 1] = mk2(-a[r + 8].x, -a[r + 8].y);
+    }
+  }
+  DftStage<16, SIGN, 4, C2>::run(b);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = b[i];
+}
+
 // FFT of nl lines of length n held in shared (or global) memory:
 // element e of line l at buf[l*ls + e*es].  tw[t2*A + k1] = exp(-2 pi i t2 k1 / n).
 // SIGN < 0: forward, natural -> permuted.  SIGN > 0: inverse, permuted -> natural.

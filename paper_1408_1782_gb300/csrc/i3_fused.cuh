@@ -346,6 +346,80 @@ __device__ __forceinline__ void wl_rows_stage_b(float2* G, int w, int lane) {
   }
 }
 
+// The shifted pair S = S_jm(w_p) (eq. approxH-JM's spectral shift: the phase-multiplied Xi
+// coefficients of `in`, inverse 2-D transform) into S[x n + y] (natural order) on the warp-local
+// passes.  The coefficients are zero outside Xi x Xi, a quarter of the padded grid: in the permuted
+// order a stage-B line of 16 holds Xi frequencies at t = 0..3, 12..15 only, so the rows are
+// transformed first and only the four Xi rows of each warp (stage B with its first radix-2 stage
+// reduced, stage A), then every column from those rows alone (stage B reduced in the same way, stage
+// A storing S, coalesced along y).  The other rows of G are not touched.  Ends with a block barrier:
+// S is complete for every thread and G is free.
+__device__ __forceinline__ void wl_shift(float2* G, const float2* tw, const float2* twT, const float2* in,
+                                         const float2* px, const float2* py, float2* S, int w, int lane, int g,
+                                         int tt) {
+  using C2 = float2;
+  constexpr int n = kWlN, A = Split<n>::A, B = Split<n>::B;
+  static_assert(A == 8 && B == 16, "Xi pattern of the 8 x 16 split");
+  const int xr0 = 8 * w + 4 * (w & 1);   // this warp's Xi rows: x mod 16 in 0..3 or 12..15
+  {
+    const int x = xr0 + (lane & 3), k1 = lane >> 2;
+    const C2 pxx = px[x];
+    C2 b[B];
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+      if (t < 4 || t >= 12) {
+        const int y = B * k1 + t;
+        b[t] = cmul(in[x * n + y], cmul(pxx, py[y]));
+      } else {
+        b[t] = zero2<float>();
+      }
+    }
+    dft16_xi<1>(b);
+#pragma unroll
+    for (int t = 0; t < B; ++t) G[wl_addr(x, B * k1 + t)] = b[t];
+  }
+  __syncwarp();
+  const int t2r = lane & 15;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int x = xr0 + (lane >> 4) + 2 * i;
+    C2 v[A];
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) v[k1] = G[wl_addr(x, B * k1 + t2r)];
+#pragma unroll
+    for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2r]);
+    dft<A, 1>(v);
+#pragma unroll
+    for (int t1 = 0; t1 < A; ++t1) G[wl_addr(x, B * t1 + t2r)] = v[t1];
+  }
+  __syncthreads();
+  const int y = 16 * g + (tt & 15);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int k1 = (tt >> 4) + 4 * i;
+    C2 b[B];
+#pragma unroll
+    for (int t = 0; t < B; ++t) b[t] = (t < 4 || t >= 12) ? G[wl_addr(B * k1 + t, y)] : zero2<float>();
+    dft16_xi<1>(b);
+#pragma unroll
+    for (int t = 0; t < B; ++t) G[wl_addr(B * k1 + t, y)] = b[t];
+  }
+  wl_pair_sync(g);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int t2 = (tt >> 4) + 4 * i;
+    C2 v[A];
+#pragma unroll
+    for (int k = 0; k < A; ++k) v[k] = G[wl_addr(B * k + t2, y)];
+#pragma unroll
+    for (int k = 1; k < A; ++k) v[k] = cmulc(v[k], tw[t2 * A + k]);
+    dft<A, 1>(v);
+#pragma unroll
+    for (int k = 0; k < A; ++k) S[(B * k + t2) * n + y] = v[k];
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kWlThreads, 1) k_i3_wl(const I3Jobs<float> jobs, float2* ws,
                                                         const float2* __restrict__ gtw) {
   using C2 = float2;
@@ -356,12 +430,7 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_i3_wl(const I3Jobs<float> job
   C2* twT = tw + n;                                           // twT[k1 B + t2]
   C2* G = twT + n;                                            // skewed field
   float* psm = reinterpret_cast<float*>(G + n * kWlPitch);    // psi'_j of the current unit, [n][kWlPsiPitch]
-  __shared__ unsigned char xmask[n];
-  for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
-    const int k = freq_of_pos<n>(pos);
-    xmask[pos] = ((k < n / 4) || (k >= n - n / 4)) ? 1 : 0;
-    twT[(pos % A) * B + pos / A] = gtw[pos];
-  }
+  for (int pos = threadIdx.x; pos < n; pos += blockDim.x) twT[(pos % A) * B + pos / A] = gtw[pos];
   load_twiddles<n>(tw, gtw);
   C2* Sig = ws + (size_t)blockIdx.x * 3 * P;   // [2][P]
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = w >> 1, tt = tid & 63;
@@ -393,46 +462,9 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_i3_wl(const I3Jobs<float> job
       const C2* px = phase + ((size_t)j * M + m) * 2 * n;
       const C2* py = px + n;
       const bool first_m = (m == m0);
-      // shifted pairs: columns (stage B loads the phase-multiplied Xi coefficients), rows (stage A
-      // stores the shifted field)
-      for (int p = 0; p < 2; ++p) {
-        const C2* in = what + ((size_t)c * 4 + p) * P;
-        {
-          const int y = 16 * g + (tt & 15);
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const int k1 = (tt >> 4) + 4 * i;
-            C2 b[B];
-#pragma unroll
-            for (int t = 0; t < B; ++t) {
-              const int x = B * k1 + t;
-              b[t] = (xmask[x] && xmask[y]) ? cmul(in[x * n + y], cmul(px[x], py[y])) : zero2<float>();
-            }
-            dft<B, 1>(b);
-#pragma unroll
-            for (int t = 0; t < B; ++t) G[wl_addr(B * k1 + t, y)] = b[t];
-          }
-        }
-        wl_pair_sync(g);
-        wl_cols_stage_a<1>(G, tw, g, tt);
-        __syncthreads();
-        wl_rows_stage_b<1>(G, w, lane);
-        __syncwarp();
-        C2* S = Sig + (size_t)p * P;
-#pragma unroll
-        for (int k = 0; k < TPT; ++k) {
-          const int x = row_of(k);
-          C2 v[A];
-#pragma unroll
-          for (int k1 = 0; k1 < A; ++k1) v[k1] = G[wl_addr(x, B * k1 + t2r)];
-#pragma unroll
-          for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2r]);
-          dft<A, 1>(v);
-#pragma unroll
-          for (int t1 = 0; t1 < A; ++t1) S[x * n + B * t1 + t2r] = v[t1];
-        }
-        __syncthreads();   // S complete (the row passes below read other warps' rows of it) and G free
-      }
+      // shifted pairs (S complete for every thread when wl_shift returns)
+      for (int p = 0; p < 2; ++p)
+        wl_shift(G, tw, twT, what + ((size_t)c * 4 + p) * P, px, py, Sig + (size_t)p * P, w, lane, g, tt);
       for (int p = 0; p < 2; ++p) {
         const C2* Sp = Sig + (size_t)p * P;      // rewritten every m: plain (coherent) loads
         C2* accp = acc + (size_t)p * P;

@@ -11,8 +11,9 @@
 // the unit's Fourier-space partials.  The sixteen convolutions are ordered by the field they feed:
 // for x = 0, 1, the four T_{2x+im,p} and the four Q_{a,x} all reach XZ_x, which is accumulated in
 // registers (every convolution's last stage gives each thread the same 32 points), and the S^T of
-// XZ_x starts from those registers, so XZ is never stored.  The shifted fields and the partials are
-// read and written only at the thread's own points, so they need no block synchronisation.
+// XZ_x starts from those registers, so XZ is never stored.  The partials are read and written only
+// at the thread's own points; the shifted fields are complete for every thread after the block
+// barrier that ends their transform.
 #pragma once
 
 // One Psi'_j convolution of the field load(idx) (idx = x * n + y) on the warp-local passes; epi(k, t1,
@@ -92,14 +93,9 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_i3_vjp_wl(
   C2* twT = tw + n;                                           // twT[k1 B + t2]
   C2* G = twT + n;                                            // skewed field
   float* psm = reinterpret_cast<float*>(G + n * kWlPitch);    // psi'_j of the current unit, [n][kWlPsiPitch]
-  __shared__ unsigned char xmask[n];
   __shared__ int kslot[n];
   __shared__ int kcols[n];
-  for (int pos = threadIdx.x; pos < n; pos += blockDim.x) {
-    const int k = freq_of_pos<n>(pos);
-    xmask[pos] = ((k < n / 4) || (k >= n - n / 4)) ? 1 : 0;
-    twT[(pos % A) * B + pos / A] = gtw[pos];
-  }
+  for (int pos = threadIdx.x; pos < n; pos += blockDim.x) twT[(pos % A) * B + pos / A] = gtw[pos];
   load_twiddles<n>(tw, gtw);
   build_xi_slots<n>(kslot, kcols);
   C2* Sig = ws + (size_t)blockIdx.x * 2 * P;   // [2][P], the shifted pairs of the current m
@@ -128,46 +124,9 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_i3_vjp_wl(
       const C2* px = phase + ((size_t)j * M + m) * 2 * n;
       const C2* py = px + n;
       const bool first_m = (m == m0);
-      // shifted pairs S_p (as in k_i3_wl): column stage B loads the phase-multiplied Xi coefficients,
-      // row stage A stores the shifted field at the thread's points
-      for (int p = 0; p < 2; ++p) {
-        const C2* in = what + ((size_t)c * 4 + p) * P;
-        {
-          const int y = 16 * g + (tt & 15);
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const int k1 = (tt >> 4) + 4 * i;
-            C2 b[B];
-#pragma unroll
-            for (int t = 0; t < B; ++t) {
-              const int x = B * k1 + t;
-              b[t] = (xmask[x] && xmask[y]) ? cmul(in[x * n + y], cmul(px[x], py[y])) : zero2<float>();
-            }
-            dft<B, 1>(b);
-#pragma unroll
-            for (int t = 0; t < B; ++t) G[wl_addr(B * k1 + t, y)] = b[t];
-          }
-        }
-        wl_pair_sync(g);
-        wl_cols_stage_a<1>(G, tw, g, tt);
-        __syncthreads();
-        wl_rows_stage_b<1>(G, w, lane);
-        __syncwarp();
-        C2* S = Sig + (size_t)p * P;
-#pragma unroll
-        for (int k = 0; k < TPT; ++k) {
-          const int x = row_of(k);
-          C2 v[A];
-#pragma unroll
-          for (int k1 = 0; k1 < A; ++k1) v[k1] = G[wl_addr(x, B * k1 + t2r)];
-#pragma unroll
-          for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(v[k1], twT[k1 * B + t2r]);
-          dft<A, 1>(v);
-#pragma unroll
-          for (int t1 = 0; t1 < A; ++t1) S[x * n + B * t1 + t2r] = v[t1];
-        }
-        __syncthreads();   // G's columns are rewritten by the next column stage of another pair
-      }
+      // shifted pairs S_p (as in k_i3_wl; S complete for every thread when wl_shift returns)
+      for (int p = 0; p < 2; ++p)
+        wl_shift(G, tw, twT, what + ((size_t)c * 4 + p) * P, px, py, Sig + (size_t)p * P, w, lane, g, tt);
       for (int x = 0; x < 2; ++x) {
         C2 racc[TPT][A];   // XZ_x at the thread's points
 #pragma unroll
