@@ -328,11 +328,11 @@ __global__ void __launch_bounds__(NTH, MINB)
         const C2* in = what + ((size_t)c * 4 + p) * P;
         C2* S = Sig + (size_t)p * P;
         // only the n/2 columns (y frequencies) of Xi are non-zero: transform those
-        col_pass_list<n, 1, false, 0, CB>(
+        col_pass_list<n, 1, false, 0, CB, true>(
             sm, tw, xcols, n / 2,
             [&](int ix, int iy) { return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<T>(); },
             NoMid(), [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
-        row_pass<n, 1, false, 0, CB>(
+        row_pass<n, 1, false, 0, CB, true>(
             sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : zero2<T>(); }, NoMid(),
             [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
       }
@@ -428,8 +428,8 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_smem(const I3Jobs<floa
           G[ix * LS + iy] = (xmask[ix] && xmask[iy]) ? cmul(in[idx], cmul(px[ix], py[iy])) : zero2<float>();
         }
         __syncthreads();
-        fft_lines<n, 1>(G, n, 1, LS, tw);     // columns (along ix)
-        fft_lines<n, 1>(G, n, LS, 1, tw);     // rows (along iy)
+        fft_lines<n, 1, true>(G, n, 1, LS, tw);     // columns (along ix), input zero outside Xi
+        fft_lines<n, 1, true>(G, n, LS, 1, tw);     // rows (along iy), zero outside the Xi columns
         C2* S = Sig + (size_t)p * P;
         for (int idx = threadIdx.x; idx < P; idx += blockDim.x) S[idx] = G[(idx / n) * LS + idx % n];
         __syncthreads();
@@ -771,7 +771,7 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(NT, 1)
           F[idx] = xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<float>();
         }
         __syncthreads();
-        fft_lines<n, 1>(F, XC, 1, XC, tw);
+        fft_lines<n, 1, true>(F, XC, 1, XC, tw);
         #pragma unroll 1
         for (int idx = tid; idx < n * XC; idx += NT) {
           const int ix = idx / XC, cc = idx % XC;
@@ -790,7 +790,7 @@ __global__ void __cluster_dims__(kI3Cluster, 1, 1) __launch_bounds__(NT, 1)
           F[r * LS + iy] = xmask[iy] ? __ldcg(&S[idx]) : zero2<float>();
         }
         __syncthreads();
-        fft_lines<n, 1>(F, R, LS, 1, tw);
+        fft_lines<n, 1, true>(F, R, LS, 1, tw);
         #pragma unroll 1
         for (int idx = tid; idx < R * n; idx += NT) S[idx] = F[(idx / n) * LS + idx % n];
         __syncthreads();

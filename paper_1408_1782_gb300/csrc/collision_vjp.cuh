@@ -457,11 +457,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_i3_vjp(
       for (int p = 0; p < 2; ++p) {
         const C2* in = what + ((size_t)c * 4 + p) * P;
         C2* S = Sig + (size_t)p * P;
-        col_pass_list<n, 1, false, 0>(
+        col_pass_list<n, 1, false, 0, 65536, true>(
             sm, tw, xcols, n / 2,
             [&](int ix, int iy) { return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<T>(); },
             NoMid(), [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
-        row_pass<n, 1, false, 0>(
+        row_pass<n, 1, false, 0, 65536, true>(
             sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : zero2<T>(); }, NoMid(),
             [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
       }
@@ -609,8 +609,8 @@ __global__ void __launch_bounds__(kThreadsI3Smem, 1) k_i3_vjp_smem(
           G[ix * LS + iy] = (xmask[ix] && xmask[iy]) ? cmul(in[idx], cmul(px[ix], py[iy])) : zero2<float>();
         }
         __syncthreads();
-        fft_lines<n, 1>(G, n, 1, LS, tw);
-        fft_lines<n, 1>(G, n, LS, 1, tw);
+        fft_lines<n, 1, true>(G, n, 1, LS, tw);   // shifts: input zero outside Xi x Xi
+        fft_lines<n, 1, true>(G, n, LS, 1, tw);
         C2* S = Sig + (size_t)p * P;
         for (int idx = threadIdx.x; idx < P; idx += blockDim.x) S[idx] = G[(idx / n) * LS + idx % n];
         __syncthreads();

@@ -256,11 +256,20 @@ __device__ __forceinline__ void dft16_xi(C2 (&a)[16]) {
   for (int i = 0; i < 16; ++i) a[i] = b[i];
 }
 
+// Padded grids whose stage-B lines (B = 16) hold the band-limited frequencies |k| < n/4 (Xi) at
+// t = 0..3, 12..15 only: n = A B with n / 4 = 4 A.
+template <int n>
+__host__ __device__ constexpr bool xi_prunable() {
+  return Split<n>::B == 16;
+}
+
 // FFT of nl lines of length n held in shared (or global) memory:
 // element e of line l at buf[l*ls + e*es].  tw[t2*A + k1] = exp(-2 pi i t2 k1 / n).
 // SIGN < 0: forward, natural -> permuted.  SIGN > 0: inverse, permuted -> natural.
+// XI (inverse only): the input is zero outside Xi, so where xi_prunable<n>() the first stage reads
+// the Xi values of each line only and runs dft16_xi.
 // Must be called by every thread of the block; ends with __syncthreads().
-template <int n, int SIGN, class C2>
+template <int n, int SIGN, bool XI = false, class C2>
 __device__ __forceinline__ void fft_lines(C2* buf, int nl, int ls, int es, const C2* __restrict__ tw) {
   constexpr int A = Split<n>::A, B = Split<n>::B;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -294,9 +303,15 @@ __device__ __forceinline__ void fft_lines(C2* buf, int nl, int ls, int es, const
       const int l = task % nl, k1 = task / nl;
       C2* base = buf + l * ls + B * k1 * es;
       C2 b[B];
+      if constexpr (XI && xi_prunable<n>()) {
 #pragma unroll
-      for (int k2 = 0; k2 < B; ++k2) b[k2] = base[k2 * es];
-      dft<B, 1>(b);
+        for (int k2 = 0; k2 < B; ++k2) b[k2] = (k2 < 4 || k2 >= 12) ? base[k2 * es] : mk2((typename RealOf<C2>::type)0, (typename RealOf<C2>::type)0);
+        dft16_xi<1>(b);
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) b[k2] = base[k2 * es];
+        dft<B, 1>(b);
+      }
 #pragma unroll
       for (int t2 = 0; t2 < B; ++t2) base[t2 * es] = b[t2];
     }
@@ -386,7 +401,8 @@ template <int n, int ELEM = 16, int CB = 65536> struct Chunk {
 // Row pass over an n x n field (rows = fixed ix, transform along iy):
 // for each chunk: sm[r][iy] = ld(ix, iy); [FFT DIR1]; [sm = mid(ix, iy, sm)]; [FFT DIR2]; st(ix, iy, sm).
 // DIR = 0 skips that transform; HAS_MID selects the pointwise middle step.
-template <int n, int DIR1, bool HAS_MID, int DIR2, int CB = 65536, class C2, class LD, class MID, class ST>
+template <int n, int DIR1, bool HAS_MID, int DIR2, int CB = 65536, bool XI = false, class C2, class LD, class MID,
+          class ST>
 __device__ __forceinline__ void row_pass(C2* sm, const C2* tw, LD ld, MID mid, ST st) {
   constexpr int RC = Chunk<n, sizeof(C2), CB>::RC, LS = Chunk<n, sizeof(C2), CB>::LS;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -397,7 +413,7 @@ __device__ __forceinline__ void row_pass(C2* sm, const C2* tw, LD ld, MID mid, S
       sm[r * LS + iy] = ld(r0 + r, iy);
     }
     __syncthreads();
-    if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1)>(sm, RC, LS, 1, tw);
+    if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1), XI>(sm, RC, LS, 1, tw);
     if (HAS_MID) {
   #pragma unroll 4
     for (int idx = tid; idx < RC * n; idx += nt) {
@@ -471,7 +487,8 @@ __device__ __forceinline__ void col_conv_pass(C2* sm, const C2* tw, LD ld, MUL m
 }
 
 // Column pass over a subset of columns cols[0..ncols) (chunks of CC columns).
-template <int n, int DIR1, bool HAS_MID, int DIR2, int CB = 65536, class C2, class LD, class MID, class ST>
+template <int n, int DIR1, bool HAS_MID, int DIR2, int CB = 65536, bool XI = false, class C2, class LD, class MID,
+          class ST>
 __device__ __forceinline__ void col_pass_list(C2* sm, const C2* tw, const int* cols, int ncols, LD ld, MID mid,
                                               ST st) {
   constexpr int CC = Chunk<n, sizeof(C2), CB>::CC;
@@ -484,7 +501,7 @@ __device__ __forceinline__ void col_pass_list(C2* sm, const C2* tw, const int* c
       sm[ix * CC + c] = ld(ix, cols[c0 + c]);
     }
     __syncthreads();
-    if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1)>(sm, nc, 1, CC, tw);
+    if (DIR1 != 0) fft_lines<n, (DIR1 < 0 ? -1 : 1), XI>(sm, nc, 1, CC, tw);
     if (HAS_MID) {
   #pragma unroll 4
     for (int idx = tid; idx < nc * n; idx += nt) {

@@ -64,11 +64,11 @@ __global__ void __launch_bounds__(NTH, MINB)
       for (int p = 0; p < 2; ++p) {
         const C2* in = what + ((size_t)c * 4 + p) * P;
         C2* S = Sig + (size_t)p * P;
-        col_pass_list<n, 1, false, 0, CB>(
+        col_pass_list<n, 1, false, 0, CB, true>(
             sm, tw, xcols, n / 2,
             [&](int ix, int iy) { return xmask[ix] ? cmul(in[ix * n + iy], cmul(px[ix], py[iy])) : zero2<T>(); },
             NoMid(), [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
-        row_pass<n, 1, false, 0, CB>(
+        row_pass<n, 1, false, 0, CB, true>(
             sm, tw, [&](int ix, int iy) { return xmask[iy] ? S[ix * n + iy] : zero2<T>(); }, NoMid(),
             [&](int ix, int iy, C2 v) { S[ix * n + iy] = v; });
       }
