@@ -53,9 +53,9 @@ FP32_FMA_PER_CLK_PER_SM = 128        # measured 122 FFMA lanes/clk/SM (the same 
 # DRAM bytes (read + write) per (cell, j, m) unit of the default I3 kernel from one ncu capture of a
 # slice (8 cells at N = 64: k_i3_sf in FP64, k_i3_wl in FP32; 4 cells at N = 128: k_i3_cluster in its
 # register-accumulating shape), scaled by units; absent for sizes with no capture of the current kernel.
-I3_DRAM_BYTES_PER_UNIT = {(64, 0): 113.540e9 / 8192, (64, 1): 3.080e9 / 8192, (128, 1): 15.105e9 / 4096}
+I3_DRAM_BYTES_PER_UNIT = {(64, 0): 113.013e9 / 8192, (64, 1): 3.090e9 / 8192, (128, 1): 15.160e9 / 4096}
 # The same for the default I3 transpose kernel (8 cells at N = 64: k_i3_vjp_wl, one cotangent).
-I3_VJP_DRAM_BYTES_PER_UNIT = {(64, 1): 5.942e9 / 8192}
+I3_VJP_DRAM_BYTES_PER_UNIT = {(64, 1): 5.463e9 / 8192}
 
 
 def workload(name="plain_fp64_n64", precision=None):
